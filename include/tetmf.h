@@ -1,0 +1,206 @@
+/*
+ * tetmf — matrix-free Laplace/Poisson operators on affine tetrahedral meshes
+ * (continuous P_p and SIPG discontinuous P_p), GB300 / sm_103a.
+ *
+ * C ABI.  Every entry point returns an int status (FEM_OK == 0 on success);
+ * the text of the last error of the calling thread is available from
+ * fem_last_error().  No C++ exception crosses this boundary.  Pointers are
+ * plain host or device addresses as stated per argument; nothing here
+ * refers to PyTorch.
+ *
+ * Operation (arxiv 2509.10226, Sec. 2.2, Eq. 3):
+ *     y = A(u) = sum_e G_e^T E^T D_e E G_e u
+ * G_e gathers the cell's DoF values, E (Eq. 4) holds the reference gradients
+ * of the shape functions at the quadrature points, D_e applies J^-T, the
+ * quadrature weight times |det J| (times the optional coefficient k_q) and
+ * J^-1, E^T integrates back and G_e^T scatter-adds.  For the discontinuous
+ * space (Eq. 2, Eq. 5) a face loop adds the SIPG flux terms.
+ *
+ * Conventions fixed by this library (the paper leaves them open):
+ *   - quadrature: Grundmann-Moeller with s = p on cells (nq = 5/15/35/70 for
+ *     p = 1..4) and on faces (nqf = 4/10/20/35); point order i ascending then
+ *     beta lexicographic ascending; coefficient arrays k/dk use this order;
+ *   - J = [x1-x0 | x2-x0 | x3-x0] from the user's vertex order of each cell;
+ *     |det J| is used, so either orientation is accepted;
+ *   - local shape-function order: beta in N^4, |beta| = p, lexicographic
+ *     ascending, node (beta_1, beta_2, beta_3)/p on the reference cell;
+ *   - SIPG: face owner K^- = adjacent cell with the smaller user id, n the unit
+ *     normal out of K^-; tau_F = eta / h_F with h_F = min_K 3|K|/|F| and
+ *     eta = (p+1)(p+3) unless given; boundary faces are homogeneous Dirichlet
+ *     by the mirror principle (u+ = -u-, grad u+ = grad u-);
+ *   - CG Dirichlet (optional): DoFs whose vertices lie on one boundary face
+ *     are constrained; the operator is P A P + (I - P) (identity rows).
+ *
+ * Numbering.  The library renumbers cells (Morton order of centroids unless
+ * reorder = FEM_REORDER_NONE) and DoFs (first touch in cell order).  Vectors
+ * passed to the hot calls are in library order; fem_dof_permutation and
+ * fem_cell_permutation translate.  Coefficients k and dk are [n_cells][nq]
+ * row-major in library cell order.
+ *
+ * Streams.  Hot calls are asynchronous on the caller's CUDA stream, passed as
+ * void* (a cudaStream_t; NULL = legacy default stream).  They allocate
+ * nothing and never synchronise, except fem_solve (blocking, see there).
+ * Vector pointers of hot calls are caller-owned device memory of the
+ * context's device.  A context is not thread-safe; distinct contexts are
+ * independent.
+ */
+#ifndef TETMF_H
+#define TETMF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define FEM_OK 0
+#define FEM_EINVAL 1        /* bad argument: null pointer, size, enum value  */
+#define FEM_EMESH 2         /* degenerate cell, vertex id out of range,      */
+                            /* face shared by more than two cells            */
+#define FEM_EUNSUPPORTED 3  /* degree outside 1..4, precision not offered    */
+#define FEM_ECUDA 4         /* a CUDA runtime call or kernel launch failed   */
+#define FEM_ENOTCONV 5      /* solver hit its iteration cap                  */
+#define FEM_ENOMEM 6        /* host or device allocation failed (set-up)     */
+
+/* ---- enums ----------------------------------------------------------- */
+#define FEM_CG 0
+#define FEM_DG 1
+
+/* arithmetic of the interpolation products; vectors are double for FEM_FP64
+ * and float for every other value */
+#define FEM_FP64 0   /* FP64 FMA units                                      */
+#define FEM_FP32 1   /* FP32 FMA units                                      */
+#define FEM_TF32 2   /* tcgen05 tensor cores, TF32 operands, FP32 accumulate */
+#define FEM_BF16 3   /* tcgen05 tensor cores, BF16 operands, FP32 accumulate */
+
+#define FEM_REORDER_NONE 0
+#define FEM_REORDER_MORTON 1
+
+#define FEM_SOLVE_FP64_PCG 0   /* Jacobi-PCG, FP64 operator and vectors      */
+#define FEM_SOLVE_IR_MIXED 1   /* FP64 iterative refinement around an inner  */
+                               /* FP32-vector Jacobi-PCG (inner_prec apply)  */
+
+typedef struct fem_ctx fem_ctx;
+
+/* Mesh, host memory, copied by fem_create (the caller may free it after). */
+typedef struct {
+  int64_t n_vertices;
+  const double* xyz;      /* [n_vertices][3]                                */
+  int64_t n_cells;
+  const int32_t* cells;   /* [n_cells][4] vertex ids, user vertex order     */
+} fem_mesh_desc;
+
+typedef struct {
+  int32_t kind;              /* FEM_CG or FEM_DG                             */
+  int32_t degree;            /* p in 1..4                                    */
+  int32_t dirichlet;         /* CG only: 0 none (pure Neumann), 1 homogeneous */
+                             /* Dirichlet on the whole boundary              */
+  int32_t reorder;           /* FEM_REORDER_MORTON (default) or _NONE        */
+  double dg_penalty_factor;  /* eta; <= 0 selects (p+1)(p+3)                 */
+  int32_t device;            /* CUDA device ordinal; -1 builds a host-only   */
+                             /* plan: queries work, hot calls return EINVAL  */
+} fem_space_desc;
+
+/* ---- set-up (synchronous) ------------------------------------------ */
+
+/* Validate the mesh, build the plan (reordering, DoF numbering, geometry,
+ * reference tables, faces) in FP64 on the host and upload it to `device`.
+ * Sec. 2.3-2.5.  On success *out owns every internal buffer.
+ * Errors: EINVAL (null pointers, n_cells < 1, bad enum), EUNSUPPORTED
+ * (degree), EMESH (vertex id out of range, |det J| <= 1e-12 * (longest edge)^3,
+ * non-manifold face), ENOMEM, ECUDA. */
+int fem_create(const fem_mesh_desc* mesh, const fem_space_desc* space, fem_ctx** out);
+
+/* Free the context and its device buffers (synchronises the device). NULL ok. */
+int fem_destroy(fem_ctx* ctx);
+
+/* Last error message of the calling thread ("" if none).  Static storage. */
+const char* fem_last_error(void);
+
+/* ---- queries (host, synchronous) ----------------------------------- */
+int fem_num_dofs(const fem_ctx* ctx, int64_t* n);         /* global DoFs N   */
+int fem_num_cells(const fem_ctx* ctx, int64_t* n);
+int fem_dofs_per_cell(const fem_ctx* ctx, int32_t* nd);   /* (p+1)(p+2)(p+3)/6 */
+int fem_num_qpoints(const fem_ctx* ctx, int32_t* nq);     /* cell rule size  */
+int fem_num_faces(const fem_ctx* ctx, int64_t* interior, int64_t* boundary);
+
+/* lib_to_user[c] = user id of library cell c; array of n_cells. */
+int fem_cell_permutation(const fem_ctx* ctx, int32_t* lib_to_user);
+
+/* lib_to_canonical[i] = canonical number of library DoF i; array of N.
+ * CG canonical order: lexicographic order of the DoF keys (below).
+ * DG canonical number: user_cell * nd + local index. */
+int fem_dof_permutation(const fem_ctx* ctx, int64_t* lib_to_canonical);
+
+/* CG only: keys[i][0..p-1] = sorted user vertex ids whose mean is the node of
+ * library DoF i (vertex v_m of a cell repeated beta_m times).  Array N*p. */
+int fem_dof_keys(const fem_ctx* ctx, int32_t* keys);
+
+/* CG only: mask[i] = 1 if library DoF i is Dirichlet-constrained.  Array N. */
+int fem_dirichlet_mask(const fem_ctx* ctx, uint8_t* mask);
+
+/* ---- hot calls (asynchronous on `stream`, allocate nothing) -------- */
+
+/* y = A(k) u.  u, y: device vectors of N values (double for FEM_FP64, float
+ * otherwise), library order, must not alias.  k: NULL (k = 1) or device
+ * [n_cells][nq] of the vector type.  Eq. 3 (CG), Eq. 5 (DG).  DG supports
+ * FEM_FP64 and FEM_FP32 with k = NULL.  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k, void* stream);
+
+/* out = A(k)^T g (the transposed chain G^T E^T D^T E G; D_e is symmetric).
+ * Same arguments and layouts as fem_apply. */
+int fem_apply_adjoint(fem_ctx* ctx, int32_t prec, const void* g, void* out, const void* k, void* stream);
+
+/* Backward of L = <g, A(k) u> for CG, in one pass over the cells:
+ * grad_u = A(k)^T g (N values) and dk[e][q] = w_q |det J_e| (grad u . grad g)
+ * at quadrature point q of library cell e ([n_cells][nq]).  FEM_FP64 or
+ * FEM_FP32.  grad_u and dk must not alias the inputs. */
+int fem_coeff_grad(fem_ctx* ctx, int32_t prec, const void* u, const void* g, const void* k,
+                   void* grad_u, void* dk, void* stream);
+
+/* d = diag(A(k)) (Jacobi), N values; Dirichlet rows give 1.  FP64 or FP32. */
+int fem_diagonal(fem_ctx* ctx, int32_t prec, void* d, const void* k, void* stream);
+
+/* b_i = int f phi_i for a constant f (CG; FP64; Dirichlet entries 0). */
+int fem_rhs_const(fem_ctx* ctx, double f, double* b, void* stream);
+
+/* ---- assembled comparator (Sec. 3.2) ------------------------------- */
+
+/* Assemble the same operator as a CSR matrix on the device (CG only;
+ * allocates, synchronous).  *nnz receives the number of stored entries. */
+int fem_csr_build(fem_ctx* ctx, int64_t* nnz);
+
+/* y = A u with the assembled CSR matrix (FEM_FP64 or FEM_FP32 values). */
+int fem_csr_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, void* stream);
+
+/* ---- solve (blocking) ---------------------------------------------- */
+typedef struct {
+  int32_t mode;          /* FEM_SOLVE_FP64_PCG or FEM_SOLVE_IR_MIXED         */
+  int32_t inner_prec;    /* IR: FEM_FP32, FEM_TF32 or FEM_BF16 inner apply   */
+  double rtol;           /* stop when ||b - A x|| / ||b|| <= rtol (FP64)     */
+  double inner_rtol;     /* IR: relative reduction asked of each inner solve */
+  int32_t max_outer;     /* IR outer iterations cap                          */
+  int32_t max_inner;     /* PCG iterations cap (per inner solve for IR)      */
+} fem_solve_opts;
+
+typedef struct {
+  int32_t outer_iterations;
+  int32_t inner_iterations;  /* total PCG iterations                        */
+  double rel_residual;       /* final ||b - A x|| / ||b|| computed in FP64   */
+  double seconds;
+} fem_solve_stats;
+
+/* Solve A x = b (CG; Dirichlet spaces give an SPD operator).  b, x: device
+ * double[N]; x holds the initial guess on entry and the last iterate on
+ * return.  Work vectors are allocated by the context on the first call and
+ * kept.  Runs on `stream` and synchronises it.  Returns FEM_ENOTCONV (x still
+ * valid, stats filled) if a cap is hit. */
+int fem_solve(fem_ctx* ctx, const fem_solve_opts* opts, const double* b, double* x,
+              fem_solve_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TETMF_H */

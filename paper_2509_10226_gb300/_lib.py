@@ -1,0 +1,111 @@
+"""ctypes declarations of the tetmf C ABI (include/tetmf.h).
+
+Argument marshalling only.  Loading fails loudly if the shared library has not
+been built; there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libtetmf.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "tetmf.h")
+
+FEM_OK, FEM_EINVAL, FEM_EMESH, FEM_EUNSUPPORTED, FEM_ECUDA, FEM_ENOTCONV, FEM_ENOMEM = range(7)
+FEM_CG, FEM_DG = 0, 1
+FEM_FP64, FEM_FP32, FEM_TF32, FEM_BF16 = 0, 1, 2, 3
+FEM_REORDER_NONE, FEM_REORDER_MORTON = 0, 1
+FEM_SOLVE_FP64_PCG, FEM_SOLVE_IR_MIXED = 0, 1
+
+STATUS_NAMES = {0: "FEM_OK", 1: "FEM_EINVAL", 2: "FEM_EMESH", 3: "FEM_EUNSUPPORTED", 4: "FEM_ECUDA",
+                5: "FEM_ENOTCONV", 6: "FEM_ENOMEM"}
+
+
+class FemError(RuntimeError):
+    def __init__(self, status, func, message):
+        super().__init__(f"{func}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("n_cells", ctypes.c_int64),
+                ("cells", ctypes.c_void_p)]
+
+
+class SpaceDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("degree", ctypes.c_int32), ("dirichlet", ctypes.c_int32),
+                ("reorder", ctypes.c_int32), ("dg_penalty_factor", ctypes.c_double), ("device", ctypes.c_int32)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("inner_prec", ctypes.c_int32), ("rtol", ctypes.c_double),
+                ("inner_rtol", ctypes.c_double), ("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("outer_iterations", ctypes.c_int32), ("inner_iterations", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "fem_create": [ctypes.POINTER(MeshDesc), ctypes.POINTER(SpaceDesc), ctypes.POINTER(ctypes.c_void_p)],
+    "fem_destroy": [_P],
+    "fem_num_dofs": [_P, _P],
+    "fem_num_cells": [_P, _P],
+    "fem_dofs_per_cell": [_P, _P],
+    "fem_num_qpoints": [_P, _P],
+    "fem_num_faces": [_P, _P, _P],
+    "fem_cell_permutation": [_P, _P],
+    "fem_dof_permutation": [_P, _P],
+    "fem_dof_keys": [_P, _P],
+    "fem_dirichlet_mask": [_P, _P],
+    "fem_apply": [_P, ctypes.c_int32, _P, _P, _P, _P],
+    "fem_apply_adjoint": [_P, ctypes.c_int32, _P, _P, _P, _P],
+    "fem_coeff_grad": [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P],
+    "fem_diagonal": [_P, ctypes.c_int32, _P, _P, _P],
+    "fem_rhs_const": [_P, ctypes.c_double, _P, _P],
+    "fem_csr_build": [_P, _P],
+    "fem_csr_apply": [_P, ctypes.c_int32, _P, _P, _P],
+    "fem_solve": [_P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(SolveStats), _P],
+}
+
+_lib = None
+
+
+def header_functions(path: str = HEADER):
+    """Names of every function the public header declares."""
+    with open(path) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\s*\*)\s*(fem_\w+)\s*\(", text, flags=re.M)))
+
+
+def lib():
+    """The loaded shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2509_10226_gb300.build` "
+                              "(the CUDA library is required; there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.fem_last_error.argtypes = []
+        L.fem_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def check(status: int, func: str):
+    if status != FEM_OK:
+        raise FemError(status, func, lib().fem_last_error().decode(errors="replace"))
+    return status
+
+
+def call(name: str, *args):
+    return check(getattr(lib(), name)(*args), name)

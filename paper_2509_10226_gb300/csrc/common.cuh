@@ -1,0 +1,70 @@
+// Helpers shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+#define TETMF_CK(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      ::tetmf::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return e_ == cudaErrorMemoryAllocation ? FEM_ENOMEM : FEM_ECUDA;                       \
+    }                                                                                        \
+  } while (0)
+
+#define TETMF_LAUNCH_CK()                                                                     \
+  do {                                                                                       \
+    cudaError_t e_ = cudaGetLastError();                                                     \
+    if (e_ != cudaSuccess) {                                                                 \
+      ::tetmf::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return FEM_ECUDA;                                                                      \
+    }                                                                                        \
+  } while (0)
+
+namespace tetmf {
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Number of SMs of the current device (cached per process for device 0..15).
+int sm_count();
+
+// Opt a kernel into more than 48 KB of dynamic shared memory (once per call site).
+template <typename K>
+inline int allow_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e != cudaSuccess) {
+      set_error("cudaFuncSetAttribute(%zu bytes of shared memory): %s", bytes, cudaGetErrorString(e));
+      return FEM_ECUDA;
+    }
+  }
+  return FEM_OK;
+}
+
+// y[i] = mask && mask[i] ? u[i] * diag_one : 0  (Dirichlet identity rows, or zero fill)
+template <typename T>
+__global__ void k_init_rows(T* __restrict__ y, const T* __restrict__ u, const uint8_t* __restrict__ mask, int64_t n,
+                            T fixed) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    T v = T(0);
+    if (mask && mask[i]) v = u ? u[i] : fixed;
+    y[i] = v;
+  }
+}
+
+template <typename T>
+inline int init_rows(T* y, const T* u, const uint8_t* mask, int64_t n, T fixed, cudaStream_t s) {
+  if (n <= 0) return FEM_OK;
+  int64_t blocks = (n + 255) / 256;
+  const int64_t cap = int64_t(sm_count()) * 8;
+  if (blocks > cap) blocks = cap;
+  k_init_rows<T><<<unsigned(blocks), 256, 0, s>>>(y, u, mask, n, fixed);
+  TETMF_LAUNCH_CK();
+  return FEM_OK;
+}
+
+}  // namespace tetmf

@@ -1,0 +1,131 @@
+// Upload of a host plan to the device and release of every device buffer.
+//
+// Device layouts (all in library cell order, tiles of kTile = 128 cells; the
+// last tile is padded):
+//   idx       int32 [ntiles][nd][128]  global DoF of local node j of the tile's
+//                                      lane-th cell; a constrained DoF d is
+//                                      stored as -1-d (masked gather, Sec. 2.4)
+//   metric    T [ntiles][6][128]       |det J| J^-1 J^-T (xx xy xz yy yz zz)
+//   tables    T packed, see tables_layout: E [nq][3][nd], w [nq], V [nq][nd],
+//             wf [nqf], Vf [4][nqf][nd], Ef [4][nqf][3][nd]
+// Structure-of-arrays per tile makes every per-cell load of a warp one
+// coalesced 128-byte (FP32) or 256-byte (FP64) transaction.
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace tetmf {
+
+int sm_count() {
+  static int cached[16] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return 152;
+  if (!cached[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+namespace {
+
+template <typename T>
+int dalloc(Ctx& c, T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return FEM_OK;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? FEM_ENOMEM : FEM_ECUDA;
+  }
+  c.allocations.push_back(q);
+  *p = static_cast<T*>(q);
+  return FEM_OK;
+}
+
+template <typename T>
+int put(Ctx& c, T** p, const std::vector<T>& h) {
+  if (int s = dalloc(c, p, h.size())) return s;
+  if (!h.empty()) TETMF_CK(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return FEM_OK;
+}
+
+template <typename D, typename S>
+std::vector<D> cast(const std::vector<S>& v) {
+  std::vector<D> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = D(v[i]);
+  return o;
+}
+
+}  // namespace
+
+int upload(Ctx& c) {
+  TETMF_CK(cudaSetDevice(c.device));
+  const int64_t T = kTile;
+  const size_t ncp = size_t(c.ntiles) * T;
+
+  if (c.kind == FEM_CG) {
+    std::vector<int32_t> idx(size_t(c.ntiles) * c.nd * T, 0);
+    for (int64_t e = 0; e < c.nc; ++e) {
+      const int64_t t = e / T, l = e % T;
+      for (int j = 0; j < c.nd; ++j) {
+        const int32_t d = c.cell_dofs[size_t(e) * c.nd + j];
+        idx[(size_t(t) * c.nd + j) * T + l] = c.mask[d] ? -1 - d : d;
+      }
+    }
+    if (int s = put(c, &c.d_idx, idx)) return s;
+    if (c.dirichlet)
+      if (int s = put(c, &c.d_mask, c.mask)) return s;
+  }
+  std::vector<double> met(ncp * 6, 0.0);
+  for (int64_t e = 0; e < c.nc; ++e) {
+    const int64_t t = e / T, l = e % T;
+    for (int a = 0; a < 6; ++a) met[(size_t(t) * 6 + a) * T + l] = c.metric[size_t(e) * 6 + a];
+  }
+  if (int s = put(c, &c.d_metric64, met)) return s;
+  if (int s = put(c, &c.d_metric32, cast<float>(met))) return s;
+  if (int s = put(c, &c.d_absdet, c.absdet)) return s;
+
+  const TableLayout L = tables_layout(c.tab);
+  std::vector<double> tab(L.total);
+  std::memcpy(&tab[L.E], c.tab.E.data(), c.tab.E.size() * sizeof(double));
+  std::memcpy(&tab[L.w], c.tab.wq.data(), c.tab.wq.size() * sizeof(double));
+  std::memcpy(&tab[L.V], c.tab.V.data(), c.tab.V.size() * sizeof(double));
+  std::memcpy(&tab[L.wf], c.tab.wqf.data(), c.tab.wqf.size() * sizeof(double));
+  std::memcpy(&tab[L.Vf], c.tab.Vf.data(), c.tab.Vf.size() * sizeof(double));
+  std::memcpy(&tab[L.Ef], c.tab.Ef.data(), c.tab.Ef.size() * sizeof(double));
+  if (int s = put(c, &c.d_tab64, tab)) return s;
+  if (int s = put(c, &c.d_tab32, cast<float>(tab))) return s;
+
+  if (c.kind == FEM_DG) {
+    if (int s = put(c, &c.d_fperm, c.tab.fperm)) return s;
+    if (int s = put(c, &c.d_fi_cell, c.fi_cell)) return s;
+    if (int s = put(c, &c.d_fi_code, c.fi_code)) return s;
+    if (int s = put(c, &c.d_fi_geo64, c.fi_geo)) return s;
+    if (int s = put(c, &c.d_fi_geo32, cast<float>(c.fi_geo))) return s;
+    if (int s = put(c, &c.d_fb_cell, c.fb_cell)) return s;
+    if (int s = put(c, &c.d_fb_code, c.fb_code)) return s;
+    if (int s = put(c, &c.d_fb_geo64, c.fb_geo)) return s;
+    if (int s = put(c, &c.d_fb_geo32, cast<float>(c.fb_geo))) return s;
+  }
+  if (c.kind == FEM_CG)
+    if (int s = tc_prepare(c)) return s;
+  TETMF_CK(cudaDeviceSynchronize());
+  return FEM_OK;
+}
+
+void release(Ctx& c) {
+  if (c.device >= 0 && !c.allocations.empty()) {
+    cudaSetDevice(c.device);
+    cudaDeviceSynchronize();
+    for (void* p : c.allocations) cudaFree(p);
+    cudaGetLastError();
+  }
+  c.allocations.clear();
+}
+
+}  // namespace tetmf

@@ -1,0 +1,113 @@
+// Internal declarations shared by the host set-up and the CUDA translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "tetmf.h"
+
+namespace tetmf {
+
+constexpr int kTile = 128;  // cells per batch: one thread (or one TMEM lane) per cell
+
+void set_error(const char* fmt, ...);
+
+// Reference-element tables built by the library (Sec. 2.2, Eq. 4).
+struct RefTables {
+  int p = 0, nd = 0, nq = 0, nqf = 0;
+  std::vector<double> xq;     // [nq][3] cell quadrature points (reference coords)
+  std::vector<double> wq;     // [nq]
+  std::vector<double> E;      // [nq][3][nd] d phi_j / d xhat_k at xq
+  std::vector<double> V;      // [nq][nd] phi_j at xq
+  std::vector<double> wqf;    // [nqf] triangle weights (sum 1/2)
+  std::vector<double> Vf;     // [4][nqf][nd] values at face points of local face m
+  std::vector<double> Ef;     // [4][nqf][3][nd] reference gradients there
+  std::vector<int32_t> fperm; // [6][nqf] face point index seen from the other side
+};
+
+void build_tables(int p, RefTables& t);
+
+struct Ctx {
+  // plan
+  int kind = FEM_CG, p = 1, nd = 4, nq = 5, nqf = 4, dirichlet = 0, reorder = 1, device = -1;
+  double penalty = 0.0;
+  int64_t nv = 0, nc = 0, ndofs = 0, ntiles = 0;
+  RefTables tab;
+  std::vector<int32_t> cell_perm;   // lib -> user
+  std::vector<int32_t> cell_dofs;   // [nc][nd] lib DoF ids (CG; unmasked)
+  std::vector<int32_t> dof_keys;    // [ndofs][p] (CG)
+  std::vector<int64_t> dof_canon;   // lib DoF -> canonical DoF
+  std::vector<uint8_t> mask;        // [ndofs] Dirichlet
+  std::vector<double> metric;       // [nc][6] |det J| J^-1 J^-T (xx, xy, xz, yy, yz, zz)
+  std::vector<double> absdet;       // [nc]
+  // DG faces (library cell ids)
+  int64_t nfi = 0, nfb = 0;
+  std::vector<int32_t> fi_cell;     // [2][nfi] minus, plus
+  std::vector<int32_t> fi_code;     // [nfi] f- | f+ << 2 | o << 4
+  std::vector<double> fi_geo;       // [8][nfi] a-(3) a+(3) 2|F| tau
+  std::vector<int32_t> fb_cell;     // [nfb]
+  std::vector<int32_t> fb_code;     // [nfb] f
+  std::vector<double> fb_geo;       // [5][nfb] a(3) 2|F| tau
+
+  // device buffers (owned)
+  int32_t* d_idx = nullptr;         // [ntiles][nd][kTile], constrained DoF -> -1-id
+  double* d_metric64 = nullptr;     // [ntiles][6][kTile]
+  float* d_metric32 = nullptr;
+  double* d_absdet = nullptr;       // [nc]
+  uint8_t* d_mask = nullptr;        // [ndofs] or null
+  double* d_tab64 = nullptr;        // packed tables, see tables_layout
+  float* d_tab32 = nullptr;
+  int32_t* d_fperm = nullptr;
+  int32_t* d_fi_cell = nullptr;
+  int32_t* d_fi_code = nullptr;
+  double* d_fi_geo64 = nullptr;
+  float* d_fi_geo32 = nullptr;
+  int32_t* d_fb_cell = nullptr;
+  int32_t* d_fb_code = nullptr;
+  double* d_fb_geo64 = nullptr;
+  float* d_fb_geo32 = nullptr;
+  // tensor-core operand images (shared-memory byte images of E^T and E)
+  void* d_tc_tf32 = nullptr;
+  void* d_tc_bf16 = nullptr;
+  // CSR comparator
+  int64_t csr_nnz = 0;
+  int64_t* d_csr_rowptr = nullptr;
+  int32_t* d_csr_col = nullptr;
+  double* d_csr_val64 = nullptr;
+  float* d_csr_val32 = nullptr;
+  // solver work space
+  void* d_work = nullptr;
+  size_t work_bytes = 0;
+
+  std::vector<void*> allocations;   // every cudaMalloc, freed by destroy
+};
+
+// Offsets (in elements) of the packed reference tables on the device.
+struct TableLayout {
+  int64_t E, w, V, wf, Vf, Ef, total;
+};
+TableLayout tables_layout(const RefTables& t);
+
+// set-up steps implemented in .cu files
+int upload(Ctx& c);
+void release(Ctx& c);
+
+// hot-call launchers (return FEM_* status)
+int cg_apply_simt(Ctx& c, int prec, const void* u, void* y, const void* k, bool transpose, void* stream);
+int cg_apply_tc(Ctx& c, int prec, const void* u, void* y, const void* k, void* stream);
+int cg_coeff_grad(Ctx& c, int prec, const void* u, const void* g, const void* k, void* grad_u, void* dk,
+                  void* stream);
+int cg_diagonal(Ctx& c, int prec, void* d, const void* k, void* stream);
+int cg_rhs_const(Ctx& c, double f, double* b, void* stream);
+int dg_apply(Ctx& c, int prec, const void* u, void* y, void* stream);
+int csr_build(Ctx& c, int64_t* nnz);
+int csr_apply(Ctx& c, int prec, const void* u, void* y, void* stream);
+int solve(Ctx& c, const fem_solve_opts* o, const double* b, double* x, fem_solve_stats* st, void* stream);
+int tc_prepare(Ctx& c);
+
+}  // namespace tetmf
+
+struct fem_ctx {
+  tetmf::Ctx c;
+};

@@ -1,0 +1,194 @@
+"""Thin PyTorch-facing wrapper over the tetmf C ABI.
+
+Every computation runs in the CUDA library; this module only passes device
+pointers (``tensor.data_ptr()``), sizes and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import call
+
+PREC = {"fp64": _lib.FEM_FP64, "fp32": _lib.FEM_FP32, "tf32": _lib.FEM_TF32, "bf16": _lib.FEM_BF16}
+
+
+def _vec_dtype(prec: str):
+    return torch.float64 if prec == "fp64" else torch.float32
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class FemSpace:
+    """A mesh + finite-element space + device plan (one fem_ctx).
+
+    xyz [nv, 3] float64 and cells [nc, 4] int32 are host arrays in the user's
+    numbering.  device = -1 builds a host-only plan (queries only).
+    """
+
+    def __init__(self, xyz, cells, kind="cg", degree=1, dirichlet=False, reorder=True, penalty=None, device=0):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        mesh = _lib.MeshDesc(xyz.shape[0], xyz.ctypes.data, cells.shape[0], cells.ctypes.data)
+        space = _lib.SpaceDesc(_lib.FEM_CG if kind == "cg" else _lib.FEM_DG, int(degree), int(bool(dirichlet)),
+                               _lib.FEM_REORDER_MORTON if reorder else _lib.FEM_REORDER_NONE,
+                               float(penalty) if penalty else 0.0, int(device))
+        h = ctypes.c_void_p()
+        call("fem_create", ctypes.byref(mesh), ctypes.byref(space), ctypes.byref(h))
+        self._h = h
+        self.kind, self.degree, self.device = kind, int(degree), int(device)
+        self.n_dofs = self._q64("fem_num_dofs")
+        self.n_cells = self._q64("fem_num_cells")
+        self.dofs_per_cell = self._q32("fem_dofs_per_cell")
+        self.n_qpoints = self._q32("fem_num_qpoints")
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        call("fem_num_faces", self._h, ctypes.byref(a), ctypes.byref(b))
+        self.n_interior_faces, self.n_boundary_faces = a.value, b.value
+
+    def _q64(self, name):
+        v = ctypes.c_int64()
+        call(name, self._h, ctypes.byref(v))
+        return v.value
+
+    def _q32(self, name):
+        v = ctypes.c_int32()
+        call(name, self._h, ctypes.byref(v))
+        return v.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.lib().fem_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- numbering -----------------------------------------------------
+    def cell_permutation(self):
+        out = np.empty(self.n_cells, dtype=np.int32)
+        call("fem_cell_permutation", self._h, out.ctypes.data)
+        return out
+
+    def dof_permutation(self):
+        out = np.empty(self.n_dofs, dtype=np.int64)
+        call("fem_dof_permutation", self._h, out.ctypes.data)
+        return out
+
+    def dof_keys(self):
+        out = np.empty((self.n_dofs, self.degree), dtype=np.int32)
+        call("fem_dof_keys", self._h, out.ctypes.data)
+        return out
+
+    def dirichlet_mask(self):
+        out = np.empty(self.n_dofs, dtype=np.uint8)
+        call("fem_dirichlet_mask", self._h, out.ctypes.data)
+        return out.astype(bool)
+
+    # ---- hot calls -------------------------------------------------------
+    def _check_vec(self, t, prec, name, n=None):
+        n = self.n_dofs if n is None else n
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == _vec_dtype(prec) and t.is_contiguous()
+                and t.numel() == n):
+            raise ValueError(f"{name}: need a contiguous CUDA tensor of {n} {_vec_dtype(prec)} values")
+
+    def _check_k(self, k, prec):
+        if k is not None:
+            self._check_vec(k, prec, "k", self.n_cells * self.n_qpoints)
+
+    def apply(self, u, k=None, prec="fp64", out=None, stream=None):
+        """y = A(k) u (library DoF order)."""
+        self._check_vec(u, prec, "u")
+        self._check_k(k, prec)
+        y = torch.empty_like(u) if out is None else out
+        call("fem_apply", self._h, PREC[prec], _ptr(u), _ptr(y), _ptr(k), _stream(stream))
+        return y
+
+    def apply_adjoint(self, g, k=None, prec="fp64", out=None, stream=None):
+        self._check_vec(g, prec, "g")
+        self._check_k(k, prec)
+        y = torch.empty_like(g) if out is None else out
+        call("fem_apply_adjoint", self._h, PREC[prec], _ptr(g), _ptr(y), _ptr(k), _stream(stream))
+        return y
+
+    def coeff_grad(self, u, g, k=None, prec="fp64", stream=None):
+        """(grad_u, dk) of L = <g, A(k) u>."""
+        self._check_vec(u, prec, "u")
+        self._check_vec(g, prec, "g")
+        self._check_k(k, prec)
+        gu = torch.empty_like(u)
+        dk = torch.empty(self.n_cells, self.n_qpoints, dtype=u.dtype, device=u.device)
+        call("fem_coeff_grad", self._h, PREC[prec], _ptr(u), _ptr(g), _ptr(k), _ptr(gu), _ptr(dk), _stream(stream))
+        return gu, dk
+
+    def diagonal(self, k=None, prec="fp64", stream=None):
+        self._check_k(k, prec)
+        d = torch.empty(self.n_dofs, dtype=_vec_dtype(prec), device=f"cuda:{self.device}")
+        call("fem_diagonal", self._h, PREC[prec], _ptr(d), _ptr(k), _stream(stream))
+        return d
+
+    def rhs_const(self, f=1.0, stream=None):
+        b = torch.empty(self.n_dofs, dtype=torch.float64, device=f"cuda:{self.device}")
+        call("fem_rhs_const", self._h, ctypes.c_double(f), _ptr(b), _stream(stream))
+        return b
+
+    def csr_build(self):
+        nnz = ctypes.c_int64()
+        call("fem_csr_build", self._h, ctypes.byref(nnz))
+        return nnz.value
+
+    def csr_apply(self, u, prec="fp64", out=None, stream=None):
+        self._check_vec(u, prec, "u")
+        y = torch.empty_like(u) if out is None else out
+        call("fem_csr_apply", self._h, PREC[prec], _ptr(u), _ptr(y), _stream(stream))
+        return y
+
+    def solve(self, b, x0=None, mode="ir", inner_prec="fp32", rtol=1e-10, inner_rtol=1e-3, max_outer=50,
+              max_inner=20000, stream=None, raise_on_notconv=True):
+        """Solve A x = b (blocking).  Returns (x, stats dict)."""
+        self._check_vec(b, "fp64", "b")
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        opts = _lib.SolveOpts(_lib.FEM_SOLVE_IR_MIXED if mode == "ir" else _lib.FEM_SOLVE_FP64_PCG, PREC[inner_prec],
+                              rtol, inner_rtol, max_outer, max_inner)
+        st = _lib.SolveStats()
+        status = _lib.lib().fem_solve(self._h, ctypes.byref(opts), _ptr(b), _ptr(x), ctypes.byref(st),
+                                      _stream(stream))
+        stats = {"outer": st.outer_iterations, "inner": st.inner_iterations, "rel_residual": st.rel_residual,
+                 "seconds": st.seconds, "converged": status == _lib.FEM_OK}
+        if status != _lib.FEM_OK and (status != _lib.FEM_ENOTCONV or raise_on_notconv):
+            _lib.check(status, "fem_solve")
+        return x, stats
+
+
+class FemApply(torch.autograd.Function):
+    """y = A(k) u with a hand-written backward (fem_coeff_grad):
+    dL/du = A(k)^T (dL/dy) and dL/dk_{e,q} = w_q |det J_e| (grad u . grad dL/dy)."""
+
+    @staticmethod
+    def forward(ctx, space: FemSpace, u, k, prec="fp64"):
+        ctx.space, ctx.prec = space, prec
+        ctx.save_for_backward(u, k)
+        return space.apply(u.contiguous(), k=None if k is None else k.contiguous(), prec=prec)
+
+    @staticmethod
+    def backward(ctx, gy):
+        u, k = ctx.saved_tensors
+        gy = gy.contiguous()
+        gu, dk = ctx.space.coeff_grad(u.contiguous(), gy, k=None if k is None else k.contiguous(), prec=ctx.prec)
+        return None, gu, (dk.reshape(k.shape) if k is not None and ctx.needs_input_grad[2] else None), None
+
+
+def fem_apply(space: FemSpace, u, k=None, prec="fp64"):
+    return FemApply.apply(space, u, k, prec)

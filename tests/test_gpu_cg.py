@@ -1,0 +1,177 @@
+"""GPU parity of the continuous operator (Eq. 3) through the C ABI against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import cg, topology
+from tests.gpu_util import TOL, assert_close, encode_keys, require_gpu, to_dev, to_host
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def make(n, p, jitter=0.2, shuffle=False, reorder=True, dirichlet=False, seed=0):
+    from paper_2509_10226_gb300.fem import FemSpace
+
+    xyz, cells = synth.kuhn_cube(n, jitter=jitter, seed=seed)
+    if shuffle:
+        xyz, cells, _ = synth.shuffle_mesh(xyz, cells, seed=4)
+    sp = FemSpace(xyz, cells, kind="cg", degree=p, dirichlet=dirichlet, reorder=reorder, device=0)
+    dofs, keys = topology.cg_numbering(cells, p)
+    return sp, xyz, cells, dofs, keys
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    require_gpu()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_config1_cg_p2_8cubed(prec):
+    """CG P2 on the 8^3 Kuhn cube (3072 cells, 24 tiles), jitter 0.2h, u ~ U[-1,1]."""
+    sp, xyz, cells, dofs, keys = make(8, 2)
+    assert sp.n_dofs == 4913
+    perm = sp.dof_permutation()
+    u = synth.uniform_vector(sp.n_dofs, synth.SEEDS["u"])
+    y_ref = cg.apply(xyz, cells, u, 2, dofs=dofs)
+    y = to_host(sp.apply(to_dev(u[perm], prec), prec=prec))
+    assert_close(y, y_ref[perm], prec, "config1")
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("reorder", [True, False])
+def test_degrees_shuffled_ragged(p, prec, reorder):
+    """3^3 cube = 162 cells: one full tile and a ragged tail of 34 cells; shuffled mesh order."""
+    sp, xyz, cells, dofs, keys = make(3, p, shuffle=True, reorder=reorder, seed=p)
+    perm = sp.dof_permutation()
+    u = synth.uniform_vector(sp.n_dofs, 1)
+    y_ref = cg.apply(xyz, cells, u, p, dofs=dofs)
+    y = to_host(sp.apply(to_dev(u[perm], prec), prec=prec))
+    assert_close(y, y_ref[perm], prec, f"p={p}")
+
+
+def test_single_cell():
+    from paper_2509_10226_gb300.fem import FemSpace
+
+    xyz = np.array([[0, 0, 0], [1, 0.1, 0], [0.2, 1, 0], [0.1, 0.3, 0.9]], dtype=float)
+    cells = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    for p in (1, 3):
+        sp = FemSpace(xyz, cells, degree=p, device=0)
+        dofs, keys = topology.cg_numbering(cells, p)
+        perm = sp.dof_permutation()
+        u = synth.uniform_vector(sp.n_dofs, 2)
+        y = to_host(sp.apply(to_dev(u[perm], "fp64")))
+        assert_close(y, cg.apply(xyz, cells, u, p, dofs=dofs)[perm], "fp64", "single cell")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_variable_coefficient_adjoint_and_gradient(prec):
+    """Config-4 structure on 6^3 (1296 cells): k ~ lognormal(0, 0.5) per quadrature point."""
+    p = 2
+    sp, xyz, cells, dofs, keys = make(6, p, seed=3)
+    perm, cperm = sp.dof_permutation(), sp.cell_permutation()
+    nq = sp.n_qpoints
+    k_user = synth.lognormal_coefficients((cells.shape[0], nq), synth.SEEDS["k"])
+    u = synth.uniform_vector(sp.n_dofs, synth.SEEDS["u"])
+    w = synth.uniform_vector(sp.n_dofs, synth.SEEDS["w"])
+    kd = to_dev(k_user[cperm].ravel(), prec)
+    ud, wd = to_dev(u[perm], prec), to_dev(w[perm], prec)
+    y = to_host(sp.apply(ud, k=kd, prec=prec))
+    assert_close(y, cg.apply(xyz, cells, u, p, k=k_user, dofs=dofs)[perm], prec, "A(k)u")
+    at = to_host(sp.apply_adjoint(wd, k=kd, prec=prec))
+    assert_close(at, cg.apply_adjoint(xyz, cells, w, p, k=k_user, dofs=dofs)[perm], prec, "A(k)^T w")
+    gu, dk = sp.coeff_grad(ud, wd, k=kd, prec=prec)
+    gu_ref, dk_ref = cg.coeff_grad(xyz, cells, u, w, p, k=k_user, dofs=dofs)
+    assert_close(to_host(gu), gu_ref[perm], prec, "grad_u")
+    assert_close(to_host(dk).reshape(-1, nq), dk_ref[cperm], prec, "dk")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_dirichlet_diag_rhs(prec):
+    p = 3
+    sp, xyz, cells, dofs, keys = make(4, p, dirichlet=True, seed=5)
+    perm = sp.dof_permutation()
+    mask = topology.dirichlet_mask(cells, p, keys)
+    assert np.array_equal(sp.dirichlet_mask(), mask[perm])
+    u = synth.uniform_vector(sp.n_dofs, 1)
+    y = to_host(sp.apply(to_dev(u[perm], prec), prec=prec))
+    assert_close(y, cg.apply(xyz, cells, u, p, dirichlet_mask=mask, dofs=dofs)[perm], prec, "dirichlet")
+    d = to_host(sp.diagonal(prec=prec))
+    assert_close(d, cg.diagonal(xyz, cells, p, sp.n_dofs, dirichlet_mask=mask, dofs=dofs)[perm], prec, "diag")
+    if prec == "fp64":
+        b = to_host(sp.rhs_const(1.0))
+        assert_close(b, cg.rhs_const(xyz, cells, p, sp.n_dofs, dirichlet_mask=mask, dofs=dofs)[perm], prec, "rhs")
+
+
+def test_autograd_function():
+    from paper_2509_10226_gb300.fem import fem_apply
+
+    p = 2
+    sp, xyz, cells, dofs, keys = make(4, p, seed=6)
+    perm, cperm = sp.dof_permutation(), sp.cell_permutation()
+    k_user = synth.lognormal_coefficients((cells.shape[0], sp.n_qpoints), 3)
+    u = synth.uniform_vector(sp.n_dofs, 1)
+    w = synth.uniform_vector(sp.n_dofs, 2)
+    ud = to_dev(u[perm], "fp64").requires_grad_(True)
+    kd = to_dev(k_user[cperm].ravel(), "fp64").requires_grad_(True)
+    wd = to_dev(w[perm], "fp64")
+    L = (fem_apply(sp, ud, kd) * wd).sum()
+    L.backward()
+    gu_ref, dk_ref = cg.coeff_grad(xyz, cells, u, w, p, k=k_user, dofs=dofs)
+    assert_close(to_host(ud.grad), gu_ref[perm], "fp64", "autograd u")
+    assert_close(to_host(kd.grad).reshape(-1, sp.n_qpoints), dk_ref[cperm], "fp64", "autograd k")
+    # central differences of L in one coefficient, through the GPU forward (exact: L is linear in k)
+    e = int(np.argmax(np.abs(dk_ref[cperm]).ravel()))
+    with torch.no_grad():
+        kp, km = kd.detach().clone(), kd.detach().clone()
+        kp[e] += 1e-6
+        km[e] -= 1e-6
+        fd = ((sp.apply(ud.detach(), k=kp) - sp.apply(ud.detach(), k=km)) @ wd).item() / 2e-6
+    assert abs(fd - kd.grad[e].item()) < 1e-8 * max(1.0, abs(fd))
+
+
+def _sampled_reference(sp, xyz, cells, p, u_lib, sample, k_user=None):
+    """Oracle values of (A u) at sampled library DoFs, summed over the cells that touch each DoF."""
+    lib_keys = sp.dof_keys()
+    nv = xyz.shape[0]
+    lib_code = encode_keys(lib_keys, nv)
+    order = np.argsort(lib_code)
+    want = set(int(v) for v in np.unique(lib_keys[sample]))
+    touch = np.where(np.isin(cells, list(want)).any(axis=1))[0]
+    keys_t = topology.dof_keys(cells[touch], p)                 # oracle keys of the touching cells
+    code_t = encode_keys(keys_t.reshape(-1, p), nv)
+    lib_of = order[np.searchsorted(lib_code, code_t, sorter=order)].reshape(keys_t.shape[:2])
+    ue = u_lib[lib_of]
+    ye = cg.element_apply(xyz, cells[touch], ue, p, None if k_user is None else k_user[touch])
+    y = np.zeros(sp.n_dofs)
+    np.add.at(y, lib_of.ravel(), ye.ravel())
+    return y[sample]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
+def test_config2_full_size_sampled(prec):
+    """CG P3 on the 64^3 Kuhn cube (1,572,864 cells, 7,189,057 DoFs), Morton order, the launch the
+    benchmark times: 512 sampled rows against the oracle, plus A 1 = 0 and u^T A u = |a|^2."""
+    from paper_2509_10226_gb300.fem import FemSpace
+
+    p = 3
+    xyz, cells = synth.kuhn_cube(64, jitter=0.2, seed=synth.SEEDS["jitter"])
+    sp = FemSpace(xyz, cells, degree=p, device=0)
+    assert sp.n_dofs == 7189057
+    u = synth.uniform_vector(sp.n_dofs, synth.SEEDS["u"])  # drawn directly in library order
+    y = to_host(sp.apply(to_dev(u, prec), prec=prec))
+    rng = np.random.default_rng(11)
+    sample = rng.choice(sp.n_dofs, 512, replace=False)
+    y_ref = _sampled_reference(sp, xyz, cells, p, u, sample)
+    # the sample's scale: rows of A u are O(h) sums with cancellation; compare against the sampled max
+    assert_close(y[sample], y_ref, prec, "config2 sampled")
+    # properties that hold at any size
+    ones = to_host(sp.apply(to_dev(np.ones(sp.n_dofs), prec), prec=prec))
+    term = np.abs(y).max()
+    assert np.abs(ones).max() <= 10 * TOL[prec] * term
+    X = xyz[sp.dof_keys()].mean(axis=1)
+    a = np.array([0.3, -0.5, 0.8])
+    lin = X @ a
+    ylin = to_host(sp.apply(to_dev(lin, prec), prec=prec))
+    assert abs(lin @ ylin - a @ a) <= 10 * TOL[prec] * (a @ a) + 1e-9

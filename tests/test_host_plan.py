@@ -1,0 +1,110 @@
+"""Host-side plan of the library (device = -1, no GPU needed): numbering against
+the oracle's canonical numbering (bit-exact), Dirichlet set, reordering and the
+error paths of fem_create."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import topology
+from paper_2509_10226_gb300 import FemError, _lib
+from paper_2509_10226_gb300.fem import FemSpace
+
+
+def space(xyz, cells, **kw):
+    kw.setdefault("device", -1)
+    return FemSpace(xyz, cells, **kw)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("reorder", [True, False])
+def test_cg_numbering_matches_oracle(p, reorder):
+    xyz, cells = synth.kuhn_cube(3, jitter=0.2, seed=0)
+    xyz, cells, _ = synth.shuffle_mesh(xyz, cells, seed=4)
+    sp = space(xyz, cells, degree=p, reorder=reorder)
+    dofs, keys = topology.cg_numbering(cells, p)
+    assert sp.n_dofs == keys.shape[0]
+    assert sp.n_qpoints == [5, 15, 35, 70][p - 1]
+    perm = sp.dof_permutation()
+    assert np.array_equal(np.sort(perm), np.arange(sp.n_dofs))
+    lib_keys = sp.dof_keys()
+    assert np.array_equal(lib_keys, keys[perm])
+    cperm = sp.cell_permutation()
+    assert np.array_equal(np.sort(cperm), np.arange(cells.shape[0]))
+    if not reorder:
+        assert np.array_equal(cperm, np.arange(cells.shape[0]))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_dirichlet_mask_matches_oracle(p):
+    xyz, cells = synth.kuhn_cube(3, jitter=0.2, seed=1)
+    sp = space(xyz, cells, degree=p, dirichlet=True)
+    dofs, keys = topology.cg_numbering(cells, p)
+    mask = topology.dirichlet_mask(cells, p, keys)
+    assert np.array_equal(sp.dirichlet_mask(), mask[sp.dof_permutation()])
+
+
+def test_dg_numbering_and_faces():
+    p = 2
+    xyz, cells = synth.kuhn_cube(3, jitter=0.2, seed=2)
+    sp = space(xyz, cells, kind="dg", degree=p)
+    nd = 10
+    assert sp.n_dofs == cells.shape[0] * nd
+    cperm = sp.cell_permutation()
+    perm = sp.dof_permutation()
+    expect = (cperm[:, None].astype(np.int64) * nd + np.arange(nd)[None, :]).ravel()
+    assert np.array_equal(perm, expect)
+    interior, boundary = topology.faces(cells)
+    assert sp.n_interior_faces == interior.shape[0]
+    assert sp.n_boundary_faces == boundary.shape[0]
+
+
+def test_morton_reorder_improves_locality():
+    """Reordering a shuffled mesh makes the cells of a 128-cell batch share vertices (Sec. 2.5)."""
+    xyz, cells = synth.kuhn_cube(8, jitter=0.2, seed=0)
+    xyz, cells, _ = synth.shuffle_mesh(xyz, cells, seed=4)
+
+    def distinct_vertices_per_batch(order):
+        c = cells[order]
+        nb = len(c) // 128
+        return np.mean([len(np.unique(c[128 * b:128 * (b + 1)])) for b in range(nb)])
+
+    sp_m = space(xyz, cells, degree=1, reorder=True)
+    sp_n = space(xyz, cells, degree=1, reorder=False)
+    morton = distinct_vertices_per_batch(sp_m.cell_permutation())
+    shuffled = distinct_vertices_per_batch(sp_n.cell_permutation())
+    assert morton < 0.4 * shuffled, (morton, shuffled)
+
+
+def test_errors():
+    xyz, cells = synth.kuhn_cube(2)
+    bad = cells.copy()
+    bad[3, 2] = xyz.shape[0] + 5
+    with pytest.raises(FemError) as e:
+        space(xyz, bad, degree=1)
+    assert e.value.status == _lib.FEM_EMESH
+    flat = cells.copy()
+    flat[0] = [0, 1, 2, 2]
+    with pytest.raises(FemError) as e:
+        space(xyz, flat, degree=1)
+    assert e.value.status == _lib.FEM_EMESH
+    with pytest.raises(FemError) as e:
+        space(xyz, cells, degree=5)
+    assert e.value.status == _lib.FEM_EUNSUPPORTED
+    # a face shared by three cells
+    extra = np.vstack([cells, cells[:1]])
+    with pytest.raises(FemError) as e:
+        space(xyz, extra, degree=1)
+    assert e.value.status == _lib.FEM_EMESH
+    with pytest.raises(FemError) as e:
+        space(xyz, cells, kind="dg", degree=1, dirichlet=True)
+    assert e.value.status == _lib.FEM_EINVAL
+
+
+def test_host_only_plan_rejects_device_calls():
+    import torch
+
+    xyz, cells = synth.kuhn_cube(2)
+    sp = space(xyz, cells, degree=1)
+    L = _lib.lib()
+    assert L.fem_apply(sp._h, 0, 1, 2, None, None) == _lib.FEM_EINVAL
+    assert b"host-only" in L.fem_last_error()
