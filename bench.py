@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Operator-apply throughput of the matrix-free tetrahedral Laplacian on GB300.
+
+Workload (default): CG P3 Laplacian on the 64^3 Kuhn-split unit cube
+(1,572,864 tets, 7,189,057 DoFs), interior vertices jittered by U[-0.2h, 0.2h]
+(seed 0), Morton-ordered cells, u ~ U[-1, 1] (seed 1).  One step = one
+operator application y = A u through the C ABI (fem_apply), inputs resident in
+HBM; the L2 is flushed (a 256 MiB write) before every timed step, outside the
+timed events.  `value` is the TF32 tensor-core apply in GDoF/s (DoFs / s,
+Sec. 2.3); the FP64, FP32 and BF16 applies, the assembled CSR SpMV of the same
+operator and the DG SIPG P2 apply on the 48^3 cube are reported under
+`variants`.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs the whole workload on its own GPU (replicas;
+`value` = all ranks' DoFs / max time).
+"""
+from __future__ import annotations
+
+import os
+
+# the oracle baseline runs single-threaded; pin BLAS pools before numpy loads
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "operator-apply GDoF/s (CG P3, DG P2) FP64 vs FP32-TC, % roofline, vs CSR SpMV"
+UNIT = "GDoF/s"
+L2_FLUSH_BYTES = 256 << 20
+NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (no FP64 tensor path)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "source": "measured", "sm_max_mhz": d.get("sm_max_mhz", 2070.0)}
+    return {"hbm_gbs": 6800.0, "source": "fallback", "sm_max_mhz": 2070.0}
+
+
+def cg_bytes(C, N, nd, prec):
+    """Algorithmic bytes of one CG apply: 4 nd index bytes + the 6-entry metric per cell, u read and y written
+    once per DoF (8-byte FP64 or 4-byte FP32 values)."""
+    vb = 8 if prec == "fp64" else 4
+    return C * (4 * nd + 6 * vb) + 2 * vb * N
+
+
+def cg_flops(C, nd, nq):
+    """Flops per apply counted as in Eq. 6: 2 * (3 nq nd * 2) + (15*2 + 3) nq + nd per cell."""
+    return C * (2 * (3 * nq * nd * 2) + 33 * nq + nd)
+
+
+def dg_bytes(C, F_int, F_bnd, nd, prec):
+    """DG: one 4-byte index and the metric per cell, u read and y written per DoF, per face 2 cell ids, a code
+    word and 8 (interior) / 5 (boundary) geometry values."""
+    vb = 8 if prec == "fp64" else 4
+    return C * (4 + 6 * vb) + 2 * vb * C * nd + F_int * (12 + 8 * vb) + F_bnd * (8 + 5 * vb)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed loops run."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap,utilization.gpu")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.dev = device_index
+        self.path = os.path.join("/tmp", f"tetmf_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        loaded = [r for r in rows if (num(r[7]) or 0) > 0] or rows
+        sm = [num(r[0]) for r in loaded if num(r[0]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": num(rows[0][1]),
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(loaded),
+                "power_w_max": max((num(r[2]) or 0) for r in rows)}
+
+
+def time_steps(torch, fn, steps, warmup, flush, stream, barrier):
+    """Per-step device time (ms) with CUDA events on the launching stream; L2 flushed before every step."""
+    for _ in range(warmup):
+        flush()
+        fn()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush()
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def oracle_cpu_baseline(xyz, cells, p, N, target_s=10.0):
+    """The FP64 oracle (plain numpy cell loop, single thread) on a bounded sample of the same mesh; returns
+    its throughput scaled to whole-problem DoFs: (sample cells / s) x (N / C)."""
+    from oracle import cg, topology
+
+    C = cells.shape[0]
+
+    def run(S):
+        sub = cells[:S]
+        dofs, keys = topology.cg_numbering(sub, p)
+        u = synth.uniform_vector(keys.shape[0], 1)
+        t0 = time.perf_counter()
+        cg.apply(xyz, sub, u, p, dofs=dofs)
+        return time.perf_counter() - t0
+
+    t = run(2048)
+    S = int(min(C, max(2048, 2048 * target_s / max(t, 1e-6))))
+    t = run(S)
+    rate_cells = S / t
+    return {"value": rate_cells * N / C / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle cg.apply (gather, element loop, scatter) on the first {S} of {C} cells, "
+                      f"{t:.1f} s, scaled by N/C = {N / C:.4f} DoFs per cell"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, each step a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    xyz, cells = synth.kuhn_cube(64, jitter=0.2, seed=synth.SEEDS["jitter"])
+    from oracle import cg, topology
+
+    p = 3
+    C = cells.shape[0]
+    N = (3 * 64 + 1) ** 3
+    S = 16384
+    sub = cells[:S]
+    dofs, keys = topology.cg_numbering(sub, p)
+    u = synth.uniform_vector(keys.shape[0], 1)
+    for _ in range(args.warmup):
+        cg.apply(xyz, sub, u, p, dofs=dofs)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        cg.apply(xyz, sub, u, p, dofs=dofs)
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    value = S / t * N / C / 1e9
+    sample = (f"oracle cg.apply on the first {S} of {C} cells of the CG P3 64^3 workload per step, "
+              f"scaled by N/C = {N / C:.4f} DoFs per cell")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "CG P3 Laplacian, 64^3 Kuhn cube (1,572,864 tets, 7,189,057 DoFs), "
+                               "jitter 0.2h, FP64 oracle on a cell sample", "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=64, help="subcubes per direction of the CG workload")
+    ap.add_argument("--no-variants", action="store_true", help="time the headline apply only")
+    ap.add_argument("--no-dg", action="store_true")
+    ap.add_argument("--no-csr", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_2509_10226_gb300.fem import FemSpace
+
+    peaks = load_peaks()
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    n = args.n
+    p = 3
+    t0 = time.perf_counter()
+    xyz, cells = synth.kuhn_cube(n, jitter=0.2, seed=synth.SEEDS["jitter"])
+    sp = FemSpace(xyz, cells, kind="cg", degree=p, device=local)
+    setup_s = time.perf_counter() - t0
+    C, N, nd, nq = sp.n_cells, sp.n_dofs, sp.dofs_per_cell, sp.n_qpoints
+    u64 = torch.as_tensor(synth.uniform_vector(N, synth.SEEDS["u"]), device="cuda")
+    u32 = u64.float()
+    y64 = torch.empty_like(u64)
+    y32 = torch.empty_like(u32)
+    clocks = Clocks(local)
+    clocks.start()
+
+    # headline: TF32 tensor-core apply
+    head = "tf32"
+    ms = time_steps(torch, lambda: sp.apply(u32, prec=head, out=y32), args.steps, args.warmup, flush, stream,
+                    barrier)
+    t_head = max_over_ranks(float(np.mean(ms)))
+    value = world * N / (t_head * 1e-3) / 1e9
+    y_head = y32.double().clone()
+    hb = cg_bytes(C, N, nd, head)
+    achieved = hb / (t_head * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "fem_apply tf32 (zero-fill + k_cg_apply_tc)",
+                "peak_source": peaks["source"] + " hbm_gbs (burst copy)"}
+
+    # end to end: pinned host u -> device, apply, device -> host y, every step
+    u_h = torch.empty(N, dtype=torch.float32, pin_memory=True)
+    u_h.copy_(u32.cpu())
+    y_h = torch.empty(N, dtype=torch.float32, pin_memory=True)
+    u_dev = torch.empty_like(u32)
+
+    def e2e_step():
+        u_dev.copy_(u_h, non_blocking=True)
+        sp.apply(u_dev, prec=head, out=y32)
+        y_h.copy_(y32, non_blocking=True)
+
+    ms_e2e = time_steps(torch, e2e_step, args.steps, args.warmup, flush, stream, barrier)
+    t_e2e = max_over_ranks(float(np.mean(ms_e2e)))
+    e2e = {"value": world * N / (t_e2e * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
+           "d2h_bytes_per_step": 4 * N, "ms_per_step": t_e2e}
+
+    variants = {}
+    ref64 = None
+    if not args.no_variants:
+        vsteps = max(5, min(args.steps, 30))
+        ms64 = time_steps(torch, lambda: sp.apply(u64, prec="fp64", out=y64), vsteps, 2, flush, stream, barrier)
+        ref64 = y64.clone()
+
+        def rel(y):
+            return float(torch.linalg.norm(y.double() - ref64) / torch.linalg.norm(ref64))
+
+        t = float(np.mean(ms64))
+        fl = cg_flops(C, nd, nq)
+        variants["fp64"] = {"gdofs": N / (t * 1e-3) / 1e9, "ms": t, "bound": "alu",
+                            "achieved_tflops": fl / (t * 1e-3) / 1e12, "peak_tflops": NOMINAL_FP64_TFLOPS,
+                            "frac": fl / (t * 1e-3) / 1e12 / NOMINAL_FP64_TFLOPS, "flops_counted": "Eq. 6",
+                            "hbm_gbs": cg_bytes(C, N, nd, "fp64") / (t * 1e-3) / 1e9}
+        for prec in ("fp32", "bf16"):
+            msv = time_steps(torch, lambda: sp.apply(u32, prec=prec, out=y32), vsteps, 2, flush, stream, barrier)
+            t = float(np.mean(msv))
+            gbs = cg_bytes(C, N, nd, prec) / (t * 1e-3) / 1e9
+            variants[prec] = {"gdofs": N / (t * 1e-3) / 1e9, "ms": t, "hbm_gbs": gbs,
+                              "frac_hbm": gbs / peaks["hbm_gbs"], "rel_l2_vs_fp64": rel(y32)}
+            if prec == "fp32":
+                fmax = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+                variants[prec].update({"bound": "alu", "achieved_tflops": fl / (t * 1e-3) / 1e12,
+                                       "peak_tflops_fp32_fma": fmax})
+        variants["tf32"] = {"gdofs": value / world, "ms": t_head, "hbm_gbs": achieved,
+                            "frac_hbm": achieved / peaks["hbm_gbs"], "rel_l2_vs_fp64": rel(y_head)}
+        if not args.no_csr:
+            try:
+                t0 = time.perf_counter()
+                nnz = sp.csr_build()
+                build_s = time.perf_counter() - t0
+                for prec, u_, y_ in (("fp64", u64, y64), ("fp32", u32, y32)):
+                    msv = time_steps(torch, lambda: sp.csr_apply(u_, prec=prec, out=y_), vsteps, 2, flush, stream,
+                                     barrier)
+                    t = float(np.mean(msv))
+                    vb = 8 if prec == "fp64" else 4
+                    b = nnz * (4 + vb) + 8 * (N + 1) + 2 * vb * N
+                    gbs = b / (t * 1e-3) / 1e9
+                    variants[f"csr_{prec}"] = {"gdofs": N / (t * 1e-3) / 1e9, "ms": t, "nnz": nnz,
+                                               "hbm_gbs": gbs, "frac_hbm": gbs / peaks["hbm_gbs"],
+                                               "rel_l2_vs_fp64": rel(y_), "build_s": build_s}
+            except Exception as e:  # noqa: BLE001
+                variants["csr"] = {"unavailable": str(e).splitlines()[0]}
+        if not args.no_dg:
+            try:
+                xd, cd = synth.kuhn_cube(48, jitter=0.2, seed=synth.SEEDS["jitter"])
+                dsp = FemSpace(xd, cd, kind="dg", degree=2, device=local)
+                du64 = torch.as_tensor(synth.uniform_vector(dsp.n_dofs, synth.SEEDS["u"]), device="cuda")
+                du32 = du64.float()
+                dy64 = torch.empty_like(du64)
+                dy32 = torch.empty_like(du32)
+                for prec, u_, y_ in (("fp64", du64, dy64), ("fp32", du32, dy32)):
+                    msv = time_steps(torch, lambda: dsp.apply(u_, prec=prec, out=y_), vsteps, 2, flush, stream,
+                                     barrier)
+                    t = float(np.mean(msv))
+                    b = dg_bytes(dsp.n_cells, dsp.n_interior_faces, dsp.n_boundary_faces, 10, prec)
+                    variants[f"dg_p2_48_{prec}"] = {"gdofs": dsp.n_dofs / (t * 1e-3) / 1e9, "ms": t,
+                                                    "n_dofs": dsp.n_dofs, "hbm_gbs": b / (t * 1e-3) / 1e9}
+                variants["dg_p2_48_fp32"]["rel_l2_vs_fp64"] = float(
+                    torch.linalg.norm(dy32.double() - dy64) / torch.linalg.norm(dy64))
+                del dsp
+            except Exception as e:  # noqa: BLE001
+                variants["dg_p2_48"] = {"unavailable": str(e).splitlines()[0]}
+    clk = clocks.stop()
+    status = sp.device_status()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_cpu_baseline(xyz, cells, p, N)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_head, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "tf32", "data": "synthetic",
+            "config": {"workload": f"CG P3 Laplacian, {n}^3 Kuhn cube ({C:,} tets, {N:,} DoFs), jitter 0.2h, "
+                                   f"Morton order, u ~ U[-1,1]; TF32 tensor-core apply, FP32 vectors",
+                       "cells": C, "dofs": N, "degree": p, "quadrature": "Grundmann-Moeller s=3 (35 points)",
+                       "parallelism": f"replicas x{world}", "l2": "flushed (256 MiB write) before every step",
+                       "setup_s": setup_s},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "clocks": clk, "variants": variants, "device_status": status,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

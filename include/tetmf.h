@@ -140,6 +140,12 @@ int fem_dof_keys(const fem_ctx* ctx, int32_t* keys);
 /* CG only: mask[i] = 1 if library DoF i is Dirichlet-constrained.  Array N. */
 int fem_dirichlet_mask(const fem_ctx* ctx, uint8_t* mask);
 
+/* Device error word of the context, then reset to 0 (synchronises the
+ * device).  0 = no kernel reported a problem; bit 0 = a tensor-core kernel
+ * gave up waiting for an MMA completion (bounded wait, about 1 s) and
+ * returned without finishing its tiles.  Kernels never trap. */
+int fem_device_status(fem_ctx* ctx, int32_t* status);
+
 /* ---- hot calls (asynchronous on `stream`, allocate nothing) -------- */
 
 /* y = A(k) u.  u, y: device vectors of N values (double for FEM_FP64, float

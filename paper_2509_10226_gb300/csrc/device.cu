@@ -112,9 +112,20 @@ int upload(Ctx& c) {
     if (int s = put(c, &c.d_fb_geo64, c.fb_geo)) return s;
     if (int s = put(c, &c.d_fb_geo32, cast<float>(c.fb_geo))) return s;
   }
+  if (int s = put(c, &c.d_status, std::vector<int32_t>(4, 0))) return s;
   if (c.kind == FEM_CG)
     if (int s = tc_prepare(c)) return s;
   TETMF_CK(cudaDeviceSynchronize());
+  return FEM_OK;
+}
+
+int device_status(Ctx& c, int32_t* out) {
+  TETMF_CK(cudaDeviceSynchronize());
+  int32_t h = 0;
+  TETMF_CK(cudaMemcpy(&h, c.d_status, sizeof(h), cudaMemcpyDeviceToHost));
+  const int32_t zero = 0;
+  TETMF_CK(cudaMemcpy(c.d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+  *out = h;
   return FEM_OK;
 }
 

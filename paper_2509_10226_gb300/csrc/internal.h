@@ -76,6 +76,7 @@ struct Ctx {
   int32_t* d_csr_col = nullptr;
   double* d_csr_val64 = nullptr;
   float* d_csr_val32 = nullptr;
+  int32_t* d_status = nullptr;      // device error word (bounded waits that gave up)
   // solver work space
   void* d_work = nullptr;
   size_t work_bytes = 0;
@@ -91,6 +92,7 @@ TableLayout tables_layout(const RefTables& t);
 
 // set-up steps implemented in .cu files
 int upload(Ctx& c);
+int device_status(Ctx& c, int32_t* out);
 void release(Ctx& c);
 
 // hot-call launchers (return FEM_* status)

@@ -566,6 +566,12 @@ int fem_dirichlet_mask(const fem_ctx* ctx, uint8_t* mask) {
   return FEM_OK;
 }
 
+int fem_device_status(fem_ctx* ctx, int32_t* status) {
+  if (int s = check_device(ctx)) return s;
+  if (!status) return set_error("null output"), FEM_EINVAL;
+  return device_status(ctx->c, status);
+}
+
 int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k, void* stream) {
   if (int s = check_device(ctx)) return s;
   if (!u || !y || u == y) return set_error("fem_apply: u and y must be distinct non-null"), FEM_EINVAL;

@@ -2,11 +2,6 @@
 #include "common.cuh"
 
 namespace tetmf {
-int cg_apply_tc(Ctx&, int, const void*, void*, const void*, void*) {
-  set_error("tensor-core apply not available in this build");
-  return FEM_EUNSUPPORTED;
-}
-int tc_prepare(Ctx&) { return FEM_OK; }
 int csr_build(Ctx&, int64_t*) {
   set_error("CSR not available in this build");
   return FEM_EUNSUPPORTED;

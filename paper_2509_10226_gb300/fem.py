@@ -97,6 +97,12 @@ class FemSpace:
         call("fem_dirichlet_mask", self._h, out.ctypes.data)
         return out.astype(bool)
 
+    def device_status(self):
+        """Device error word (0 = clean), reset after reading; synchronises the device."""
+        v = ctypes.c_int32()
+        call("fem_device_status", self._h, ctypes.byref(v))
+        return v.value
+
     # ---- hot calls -------------------------------------------------------
     def _check_vec(self, t, prec, name, n=None):
         n = self.n_dofs if n is None else n

@@ -175,3 +175,37 @@ def test_config2_full_size_sampled(prec):
     lin = X @ a
     ylin = to_host(sp.apply(to_dev(lin, prec), prec=prec))
     assert abs(lin @ ylin - a @ a) <= 10 * TOL[prec] * (a @ a) + 1e-9
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_tensor_core_degrees_ragged(p, prec):
+    """tcgen05 path, p = 1..4, 3^3 cube (one full tile + a 34-cell tail), shuffled input order."""
+    sp, xyz, cells, dofs, keys = make(3, p, shuffle=True, seed=p)
+    perm = sp.dof_permutation()
+    u = synth.uniform_vector(sp.n_dofs, 1)
+    y_ref = cg.apply(xyz, cells, u, p, dofs=dofs)
+    y = to_host(sp.apply(to_dev(u[perm], prec), prec=prec))
+    assert_close(y, y_ref[perm], prec, f"p={p}")
+    assert sp.device_status() == 0
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_tensor_core_config1_variable_k_dirichlet(prec):
+    """Config-1 mesh (8^3, 24 tiles) on the tensor cores: plain, with k ~ lognormal(0, 0.5), and with
+    Dirichlet rows; several tiles per persistent CTA are exercised on the 64^3 test below."""
+    p = 2
+    sp, xyz, cells, dofs, keys = make(8, p)
+    perm, cperm = sp.dof_permutation(), sp.cell_permutation()
+    u = synth.uniform_vector(sp.n_dofs, 1)
+    y = to_host(sp.apply(to_dev(u[perm], prec), prec=prec))
+    assert_close(y, cg.apply(xyz, cells, u, p, dofs=dofs)[perm], prec, "config1")
+    k_user = synth.lognormal_coefficients((cells.shape[0], sp.n_qpoints), 3)
+    y = to_host(sp.apply(to_dev(u[perm], prec), k=to_dev(k_user[cperm].ravel(), prec), prec=prec))
+    assert_close(y, cg.apply(xyz, cells, u, p, k=k_user, dofs=dofs)[perm], prec, "variable k")
+    spd, xyz, cells, dofs, keys = make(8, p, dirichlet=True)
+    perm = spd.dof_permutation()
+    mask = topology.dirichlet_mask(cells, p, keys)
+    y = to_host(spd.apply(to_dev(u[perm], prec), prec=prec))
+    assert_close(y, cg.apply(xyz, cells, u, p, dirichlet_mask=mask, dofs=dofs)[perm], prec, "dirichlet")
+    assert sp.device_status() == 0 and spd.device_status() == 0
