@@ -4,9 +4,13 @@
 // The two dense contractions of Eq. 3 for a batch of 128 cells become GEMMs
 // ("matrix-matrix product", Sec. 2.4, with the batch extended from 4 x n_lanes
 // cells to 128 cells = the M of one tcgen05.mma):
-//   GEMM 1:  G[128 x 3nq]  = U[128 x nd]  . E^T        (E of Eq. 4, [3nq x nd])
+//   GEMM 1:  G[128 x 3nq]  = U'[128 x nd-1] . E'^T   (E' = columns 1..nd-1 of E, Eq. 4;
+//                                                     U'[m, j-1] = u_j - u_0 of cell m)
 //   D_e:     Q[m, 3q+k]    = w_q k_q (M_e G[m, 3q:3q+3])_k    per thread (row m)
-//   GEMM 2:  Y[128 x nd]   = Q[128 x 3nq] . E
+//   GEMM 2:  Y'[128 x nd-1] = Q[128 x 3nq] . E',      y_0 = -sum_{j>=1} y_j
+// The difference form is E u_e rewritten with sum_j E_j = 0 (partition of
+// unity); it is exact for exact tables and keeps rounded TF32/BF16 tables
+// consistent (constants map to zero, operand error relative to the gradient).
 // A CTA of 128 threads owns one TMEM lane per cell.  Per tile:
 //   1. each thread gathers its cell's DoFs (masked gather) and writes its row
 //      of U into shared memory in the canonical K-major no-swizzle layout;
@@ -45,10 +49,11 @@ struct TcShape {
   static constexpr int KC = 16 / ES;
   static constexpr int KSTEP = 2 * KC;
   static constexpr int N3 = 3 * NQ;
-  static constexpr int K1 = round_up(ND, KSTEP);
+  static constexpr int ND1 = ND - 1;  // DoFs 1..nd-1 enter as differences to DoF 0
+  static constexpr int K1 = round_up(ND1, KSTEP);
   static constexpr int N1 = round_up(N3, 16);
   static constexpr int K2 = round_up(N3, KSTEP);
-  static constexpr int N2 = round_up(ND, 16);
+  static constexpr int N2 = round_up(ND1, 16);
   static constexpr int COLS = pow2_cols(max_i(N1, N2));
   static constexpr int LBO_A = (kT / 8) * 128;
   static constexpr int LBO_B1 = (N1 / 8) * 128;
@@ -228,14 +233,20 @@ __global__ void __launch_bounds__(kT, 1)
     }
     // 1. masked gather of the cell's DoFs into row m of U
     int g[ND];
-    float v1[S::K1];
+    float ue[ND], v1[S::K1];
 #pragma unroll
     for (int j = 0; j < ND; ++j) {
       g[j] = active ? __ldg(idx + (tile * ND + j) * kT + m) : -1;
-      v1[j] = g[j] >= 0 ? __ldg(u + g[j]) : 0.0f;
+      ue[j] = g[j] >= 0 ? __ldg(u + g[j]) : 0.0f;
     }
+    // sum_j E_j = 0 (the gradients of a partition of unity), so E u_e equals
+    // E' (u_j - u_0)_{j >= 1} with E' the columns 1..nd-1 of E; rounding the
+    // differences and E' keeps constants in the kernel exactly and makes the
+    // operand error relative to the gradient instead of to u
 #pragma unroll
-    for (int j = ND; j < S::K1; ++j) v1[j] = 0.0f;
+    for (int j = 1; j < ND; ++j) v1[j - 1] = ue[j] - ue[0];
+#pragma unroll
+    for (int j = S::ND1; j < S::K1; ++j) v1[j] = 0.0f;
     write_row<S::K1, BF16>(sA1, m, v1);
     fence_proxy_async();
     tc_fence_before();
@@ -299,9 +310,15 @@ __global__ void __launch_bounds__(kT, 1)
     tmem_wait_ld();
 #pragma unroll
     for (int c = 0; c < S::N2 / 16; ++c) reg_fence16(r + c * 16);
+    // y_0 = -sum_{j >= 1} y_j (same identity on the test side)
+    float y0 = 0.0f;
 #pragma unroll
-    for (int j = 0; j < ND; ++j)
-      if (g[j] >= 0) atomicAdd(y + g[j], __uint_as_float(r[j]));
+    for (int j = 1; j < ND; ++j) {
+      const float yj = __uint_as_float(r[j - 1]);
+      y0 -= yj;
+      if (g[j] >= 0) atomicAdd(y + g[j], yj);
+    }
+    if (g[0] >= 0) atomicAdd(y + g[0], y0);
     tc_fence_before();
   }
   tc_fence_before();
@@ -335,12 +352,12 @@ std::vector<uint8_t> b_image(const RefTables& t) {
   auto off = [](int r, int k, int lbo) {
     return size_t((k / S::KC) * lbo + (r / 8) * 128 + (r % 8) * 16 + (k % S::KC) * S::ES);
   };
-  // B1 = E as [N1 rows = 3q+k][K1 = j]; B2 = E^T as [N2 rows = j][K2 = 3q+k]
+  // B1 = E' as [N1 rows = 3q+k][K1 = j-1]; B2 = E'^T as [N2 rows = j-1][K2 = 3q+k]
   for (int n = 0; n < S::N3; ++n)
-    for (int j = 0; j < ND; ++j) {
+    for (int j = 1; j < ND; ++j) {
       const double e = t.E[size_t(n) * ND + j];
-      put_elem<BF16>(img, off(n, j, S::LBO_B1), e);
-      put_elem<BF16>(img, S::B1_BYTES + off(j, n, S::LBO_B2), e);
+      put_elem<BF16>(img, off(n, j - 1, S::LBO_B1), e);
+      put_elem<BF16>(img, S::B1_BYTES + off(j - 1, n, S::LBO_B2), e);
     }
   return img;
 }
@@ -376,6 +393,7 @@ int launch(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) {
   const size_t sm = tc_smem<ND, NQ, BF16>(k != nullptr);
   auto kern = k_cg_apply_tc<ND, NQ, BF16>;
   if (int e = allow_smem(kern, sm)) return e;
+  TETMF_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   int per_sm = 0;
   TETMF_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT, sm));
   if (per_sm < 1) {

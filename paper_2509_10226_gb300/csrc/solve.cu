@@ -1,0 +1,375 @@
+// Poisson solve on the device: Jacobi-preconditioned CG (the smoother the paper
+// pairs with its operator is Jacobi-based, Sec. 4.1) and mixed-precision
+// iterative refinement (the paper runs its multigrid preconditioner in single
+// precision and the outer CG in double precision, Sec. 4.1):
+//
+//   x (FP64); repeat:  r = b - A_64 x              FP64 apply + residual norm
+//                      stop if ||r|| <= rtol ||b||
+//                      r32 = r / ||r||             scaled, FP32
+//                      solve A_32 d = r32 by Jacobi-PCG (FP32 vectors, FP32 or
+//                      tensor-core apply, FP64 dot products) to inner_rtol
+//                      x += ||r|| d                FP64 update
+//
+// Every reduction is a single kernel: each block writes a partial sum to a
+// scratch array, and the last block to finish (atomic ticket) adds the
+// partials in block order, so results are deterministic.  Scalars (alpha,
+// beta) stay on the device; the host reads one residual norm per iteration.
+#include <chrono>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace tetmf {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kMaxRedBlocks = 1024;
+
+// scalar slots in the solver's device scalar array
+enum : int { S_PQ = 0, S_RZ0 = 1, S_RZ1 = 2, S_RR = 3, S_NORM = 4, S_RES = 5, S_COUNT = 8 };
+
+struct Work {
+  double* scal;          // [S_COUNT]
+  double* partials;      // [kMaxRedBlocks][2]
+  unsigned* ticket;      // [1]
+  double* r64;           // [N]
+  double* t64;           // [N]
+  double* diag64;        // [N]
+  double* p64;           // [N]   (FP64 PCG)
+  double* z64;           // [N]
+  void* r;               // [N] inner vectors, FP32
+  void* z;
+  void* p;
+  void* q;
+  void* d;
+  float* diag32;
+  double* host_scal;     // pinned host mirror
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-reduce two values; the last block adds all partials and stores them
+__device__ void finish2(double v0, double v1, double* partials, unsigned* ticket, double* out0, double* out1) {
+  __shared__ double s0[kBlock / 32], s1[kBlock / 32];
+  __shared__ bool last;
+  v0 = warp_sum(v0);
+  v1 = warp_sum(v1);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    s0[w] = v0;
+    s1[w] = v1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < kBlock / 32; ++i) {
+      a += s0[i];
+      b += s1[i];
+    }
+    partials[2 * blockIdx.x] = a;
+    partials[2 * blockIdx.x + 1] = b;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < int(gridDim.x); i += kBlock) {
+    a += partials[2 * i];
+    b += partials[2 * i + 1];
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if (l == 0) {
+    s0[w] = a;
+    s1[w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int i = 0; i < kBlock / 32; ++i) {
+      x += s0[i];
+      y += s1[i];
+    }
+    if (out0) *out0 = x;
+    if (out1) *out1 = y;
+    *ticket = 0u;
+  }
+}
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < (n); i += int64_t(gridDim.x) * blockDim.x)
+
+// out0 = a . b
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_dot(const T* __restrict__ a, const T* __restrict__ b, int64_t n,
+                                                double* partials, unsigned* ticket, double* out0) {
+  double s = 0.0;
+  GRID_STRIDE(i, n) s = fma(double(a[i]), double(b[i]), s);
+  finish2(s, 0.0, partials, ticket, out0, nullptr);
+}
+
+// r = b - Ax (FP64), scal[S_RR] = r . r
+__global__ void __launch_bounds__(kBlock) k_residual64(const double* __restrict__ b, const double* __restrict__ ax,
+                                                       double* __restrict__ r, int64_t n, double* partials,
+                                                       unsigned* ticket, double* rr) {
+  double s = 0.0;
+  GRID_STRIDE(i, n) {
+    const double v = b[i] - ax[i];
+    r[i] = v;
+    s = fma(v, v, s);
+  }
+  finish2(s, 0.0, partials, ticket, rr, nullptr);
+}
+
+// inner right-hand side r32 = r64 / ||r64||, inner iterate d = 0
+__global__ void k_scale_down(const double* __restrict__ r64, const double* __restrict__ rr, float* __restrict__ r32,
+                             float* __restrict__ d, int64_t n) {
+  const double s = 1.0 / sqrt(*rr);
+  GRID_STRIDE(i, n) {
+    r32[i] = float(r64[i] * s);
+    d[i] = 0.0f;
+  }
+}
+
+// x += ||r64|| d
+__global__ void k_correct(double* __restrict__ x, const float* __restrict__ d, const double* __restrict__ rr,
+                          int64_t n) {
+  const double s = sqrt(*rr);
+  GRID_STRIDE(i, n) x[i] = fma(s, double(d[i]), x[i]);
+}
+
+// PCG start: z = r / diag, p = z, rz = r . z, rr = r . r
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_pcg_start(const T* __restrict__ r, const T* __restrict__ diag,
+                                                      T* __restrict__ z, T* __restrict__ p, int64_t n,
+                                                      double* partials, unsigned* ticket, double* rz, double* rr) {
+  double a = 0.0, b = 0.0;
+  GRID_STRIDE(i, n) {
+    const T ri = r[i];
+    const T zi = ri / diag[i];
+    z[i] = zi;
+    p[i] = zi;
+    a = fma(double(ri), double(zi), a);
+    b = fma(double(ri), double(ri), b);
+  }
+  finish2(a, b, partials, ticket, rz, rr);
+}
+
+// alpha = rz / pq; x += alpha p; r -= alpha q; z = r / diag; rz' = r . z; rr = r . r
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_pcg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
+                                                       const T* __restrict__ p, const T* __restrict__ q,
+                                                       const T* __restrict__ diag, int64_t n, const double* rz,
+                                                       const double* pq, double* partials, unsigned* ticket,
+                                                       double* rz_next, double* rr) {
+  const T alpha = T(*rz / *pq);
+  double a = 0.0, b = 0.0;
+  GRID_STRIDE(i, n) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const T ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    const T zi = ri / diag[i];
+    z[i] = zi;
+    a = fma(double(ri), double(zi), a);
+    b = fma(double(ri), double(ri), b);
+  }
+  finish2(a, b, partials, ticket, rz_next, rr);
+}
+
+// beta = rz' / rz; p = z + beta p
+template <typename T>
+__global__ void k_pcg_direction(T* __restrict__ p, const T* __restrict__ z, int64_t n, const double* rz_next,
+                                const double* rz) {
+  const T beta = T(*rz_next / *rz);
+  GRID_STRIDE(i, n) p[i] = fma(beta, p[i], z[i]);
+}
+
+template <typename T>
+__global__ void k_cast(const double* __restrict__ a, T* __restrict__ b, int64_t n) {
+  GRID_STRIDE(i, n) b[i] = T(a[i]);
+}
+
+int red_grid(int64_t n) {
+  int64_t g = (n + kBlock - 1) / kBlock;
+  const int64_t cap = std::min<int64_t>(kMaxRedBlocks, int64_t(sm_count()) * 4);
+  return int(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+int ew_grid(int64_t n) {
+  int64_t g = (n + kBlock - 1) / kBlock;
+  const int64_t cap = int64_t(sm_count()) * 8;
+  return int(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+int ensure_work(Ctx& c, Work& w) {
+  const int64_t N = c.ndofs;
+  const size_t need = sizeof(double) * (S_COUNT + 2 * kMaxRedBlocks) + 64 + sizeof(double) * 6 * N +
+                      sizeof(float) * 6 * N + 256 * 16;
+  if (c.work_bytes < need) {
+    void* p = nullptr;
+    TETMF_CK(cudaMalloc(&p, need));
+    c.allocations.push_back(p);
+    c.d_work = p;
+    c.work_bytes = need;
+    TETMF_CK(cudaMemset(p, 0, need));
+  }
+  uint8_t* b = static_cast<uint8_t*>(c.d_work);
+  auto take = [&](size_t bytes) {
+    uint8_t* r = b;
+    b += (bytes + 255) / 256 * 256;
+    return r;
+  };
+  w.scal = reinterpret_cast<double*>(take(sizeof(double) * S_COUNT));
+  w.partials = reinterpret_cast<double*>(take(sizeof(double) * 2 * kMaxRedBlocks));
+  w.ticket = reinterpret_cast<unsigned*>(take(64));
+  w.r64 = reinterpret_cast<double*>(take(sizeof(double) * N));
+  w.t64 = reinterpret_cast<double*>(take(sizeof(double) * N));
+  w.diag64 = reinterpret_cast<double*>(take(sizeof(double) * N));
+  w.p64 = reinterpret_cast<double*>(take(sizeof(double) * N));
+  w.z64 = reinterpret_cast<double*>(take(sizeof(double) * N));
+  w.r = take(sizeof(float) * N);
+  w.z = take(sizeof(float) * N);
+  w.p = take(sizeof(float) * N);
+  w.q = take(sizeof(float) * N);
+  w.d = take(sizeof(float) * N);
+  w.diag32 = reinterpret_cast<float*>(take(sizeof(float) * N));
+  static thread_local double* pinned = nullptr;
+  if (!pinned) TETMF_CK(cudaMallocHost(&pinned, sizeof(double) * S_COUNT));
+  w.host_scal = pinned;
+  return FEM_OK;
+}
+
+int read_scalar(const double* dev, double* host, double& out, cudaStream_t st) {
+  TETMF_CK(cudaMemcpyAsync(host, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  TETMF_CK(cudaStreamSynchronize(st));
+  out = *host;
+  return FEM_OK;
+}
+
+// Jacobi-PCG on vectors of type T with the operator `apply` (y = A x);
+// solves A x = r starting from x = 0 (r is overwritten by the residual).
+template <typename T, typename Apply>
+int pcg(Ctx& c, Work& w, Apply apply, T* x, T* r, T* z, T* p, T* q, const T* diag, double rtol_abs2, int max_it,
+        int& iters, cudaStream_t st) {
+  const int64_t N = c.ndofs;
+  const int rg = red_grid(N), eg = ew_grid(N);
+  k_pcg_start<T><<<rg, kBlock, 0, st>>>(r, diag, z, p, N, w.partials, w.ticket, w.scal + S_RZ0, w.scal + S_RR);
+  TETMF_LAUNCH_CK();
+  double rr = 0.0;
+  if (int e = read_scalar(w.scal + S_RR, w.host_scal, rr, st)) return e;
+  iters = 0;
+  while (rr > rtol_abs2 && iters < max_it) {
+    const int cur = S_RZ0 + (iters & 1), nxt = S_RZ0 + ((iters + 1) & 1);
+    if (int e = apply(p, q)) return e;
+    k_dot<T><<<rg, kBlock, 0, st>>>(p, q, N, w.partials, w.ticket, w.scal + S_PQ);
+    TETMF_LAUNCH_CK();
+    k_pcg_update<T><<<rg, kBlock, 0, st>>>(x, r, z, p, q, diag, N, w.scal + cur, w.scal + S_PQ, w.partials, w.ticket,
+                                           w.scal + nxt, w.scal + S_RR);
+    TETMF_LAUNCH_CK();
+    k_pcg_direction<T><<<eg, kBlock, 0, st>>>(p, z, N, w.scal + nxt, w.scal + cur);
+    TETMF_LAUNCH_CK();
+    ++iters;
+    if (int e = read_scalar(w.scal + S_RR, w.host_scal, rr, st)) return e;
+    if (!std::isfinite(rr)) {
+      set_error("fem_solve: residual is not finite after %d iterations", iters);
+      return FEM_ENOTCONV;
+    }
+  }
+  return FEM_OK;
+}
+
+}  // namespace
+
+int solve(Ctx& c, const fem_solve_opts* o, const double* b, double* x, fem_solve_stats* stats, void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = as_stream(stream);
+  Work w;
+  if (int e = ensure_work(c, w)) return e;
+  const int64_t N = c.ndofs;
+  const int rg = red_grid(N), eg = ew_grid(N);
+  *stats = fem_solve_stats{0, 0, 0.0, 0.0};
+  auto finish = [&](int status, double rel) {
+    stats->rel_residual = rel;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (status == FEM_ENOTCONV)
+      set_error("fem_solve: relative residual %.3e above rtol %.3e after %d outer / %d inner iterations", rel,
+                o->rtol, stats->outer_iterations, stats->inner_iterations);
+    return status;
+  };
+
+  double bb = 0.0;
+  k_dot<double><<<rg, kBlock, 0, st>>>(b, b, N, w.partials, w.ticket, w.scal + S_NORM);
+  TETMF_LAUNCH_CK();
+  if (int e = read_scalar(w.scal + S_NORM, w.host_scal, bb, st)) return e;
+  if (bb == 0.0) {
+    TETMF_CK(cudaMemsetAsync(x, 0, sizeof(double) * N, st));
+    TETMF_CK(cudaStreamSynchronize(st));
+    return finish(FEM_OK, 0.0);
+  }
+  if (int e = cg_diagonal(c, FEM_FP64, w.diag64, nullptr, stream)) return e;
+
+  // r64 = b - A_64 x, ||r64||^2 in scal[S_RES]; rel = ||r64|| / ||b||
+  auto residual = [&](double& rel) -> int {
+    if (int e = cg_apply_simt(c, FEM_FP64, x, w.t64, nullptr, false, stream)) return e;
+    k_residual64<<<rg, kBlock, 0, st>>>(b, w.t64, w.r64, N, w.partials, w.ticket, w.scal + S_RES);
+    TETMF_LAUNCH_CK();
+    double rr = 0.0;
+    if (int e = read_scalar(w.scal + S_RES, w.host_scal, rr, st)) return e;
+    rel = std::sqrt(rr / bb);
+    return FEM_OK;
+  };
+
+  double rel = 0.0;
+  if (o->mode == FEM_SOLVE_FP64_PCG) {
+    if (int e = residual(rel)) return e;
+    auto apply64 = [&](double* in, double* out) {
+      return cg_apply_simt(c, FEM_FP64, in, out, nullptr, false, stream);
+    };
+    int it = 0;
+    const int e = pcg<double>(c, w, apply64, x, w.r64, w.z64, w.p64, w.t64, w.diag64, o->rtol * o->rtol * bb,
+                              o->max_inner, it, st);
+    stats->inner_iterations = it;
+    stats->outer_iterations = 1;
+    if (e && e != FEM_ENOTCONV) return e;
+    if (int e2 = residual(rel)) return e2;
+    return finish(rel <= o->rtol ? FEM_OK : FEM_ENOTCONV, rel);
+  }
+
+  // mixed-precision iterative refinement
+  k_cast<float><<<eg, kBlock, 0, st>>>(w.diag64, w.diag32, N);
+  TETMF_LAUNCH_CK();
+  float* r32 = static_cast<float*>(w.r);
+  float* z32 = static_cast<float*>(w.z);
+  float* p32 = static_cast<float*>(w.p);
+  float* q32 = static_cast<float*>(w.q);
+  float* d32 = static_cast<float*>(w.d);
+  const int ip = o->inner_prec;
+  auto apply32 = [&](float* in, float* out) {
+    return ip == FEM_FP32 ? cg_apply_simt(c, FEM_FP32, in, out, nullptr, false, stream)
+                          : cg_apply_tc(c, ip, in, out, nullptr, stream);
+  };
+  const double inner = o->inner_rtol > 0 ? o->inner_rtol : 1e-3;
+  for (;;) {
+    if (int e = residual(rel)) return e;
+    if (rel <= o->rtol) return finish(FEM_OK, rel);
+    if (stats->outer_iterations >= o->max_outer) return finish(FEM_ENOTCONV, rel);
+    if (!std::isfinite(rel)) return finish(FEM_ENOTCONV, rel);
+    k_scale_down<<<eg, kBlock, 0, st>>>(w.r64, w.scal + S_RES, r32, d32, N);
+    TETMF_LAUNCH_CK();
+    int it = 0;
+    const int e = pcg<float>(c, w, apply32, d32, r32, z32, p32, q32, w.diag32, inner * inner, o->max_inner, it, st);
+    stats->inner_iterations += it;
+    stats->outer_iterations += 1;
+    if (e && e != FEM_ENOTCONV) return e;
+    k_correct<<<eg, kBlock, 0, st>>>(x, d32, w.scal + S_RES, N);
+    TETMF_LAUNCH_CK();
+  }
+}
+
+}  // namespace tetmf

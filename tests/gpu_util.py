@@ -55,3 +55,50 @@ def encode_keys(keys, nv):
     for r in range(keys.shape[1]):
         code = code * np.int64(nv) + keys[:, r]
     return code
+
+
+def sampled_rows(sp, xyz, cells, p, u_lib, sample, k_user=None, mask_lib=None):
+    """Oracle values of (A u)_i at sampled library DoFs i: the oracle's element products of every cell
+    touching a sampled DoF, gathered from and scattered to library positions found through the DoF keys.
+    With a Dirichlet mask the operator is P A P + (I - P)."""
+    from oracle import cg, topology
+
+    lib_keys = sp.dof_keys()
+    nv = xyz.shape[0]
+    lib_code = encode_keys(lib_keys, nv)
+    order = np.argsort(lib_code)
+    want = np.unique(lib_keys[sample])
+    touch = np.where(np.isin(cells, want).any(axis=1))[0]
+    keys_t = topology.dof_keys(cells[touch], p)
+    code_t = encode_keys(keys_t.reshape(-1, p), nv)
+    lib_of = order[np.searchsorted(lib_code, code_t, sorter=order)].reshape(keys_t.shape[:2])
+    ue = u_lib[lib_of]
+    if mask_lib is not None:
+        ue = np.where(mask_lib[lib_of], 0.0, ue)
+    ye = cg.element_apply(xyz, cells[touch], ue, p, None if k_user is None else k_user[touch])
+    y = np.zeros(sp.n_dofs)
+    np.add.at(y, lib_of.ravel(), ye.ravel())
+    if mask_lib is not None:
+        y[mask_lib] = u_lib[mask_lib]
+    return y[sample]
+
+
+def sampled_rhs(sp, xyz, cells, p, sample, mask_lib=None):
+    """Oracle load vector b_i = int phi_i (f = 1) at sampled library DoFs."""
+    from oracle import cg, topology
+
+    lib_keys = sp.dof_keys()
+    nv = xyz.shape[0]
+    lib_code = encode_keys(lib_keys, nv)
+    order = np.argsort(lib_code)
+    touch = np.where(np.isin(cells, np.unique(lib_keys[sample])).any(axis=1))[0]
+    keys_t = topology.dof_keys(cells[touch], p)
+    lib_of = order[np.searchsorted(lib_code, encode_keys(keys_t.reshape(-1, p), nv), sorter=order)]
+    lib_of = lib_of.reshape(keys_t.shape[:2])
+    local = np.arange(lib_of.size).reshape(lib_of.shape)
+    be = cg.rhs_const(xyz, cells[touch], p, lib_of.size, dofs=local)
+    b = np.zeros(sp.n_dofs)
+    np.add.at(b, lib_of.ravel(), be)
+    if mask_lib is not None:
+        b[mask_lib] = 0.0
+    return b[sample]

@@ -4,7 +4,7 @@ import pytest
 
 import synth
 from oracle import cg, topology
-from tests.gpu_util import TOL, assert_close, encode_keys, require_gpu, to_dev, to_host
+from tests.gpu_util import TOL, assert_close, require_gpu, sampled_rows, to_dev, to_host
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -131,24 +131,6 @@ def test_autograd_function():
     assert abs(fd - kd.grad[e].item()) < 1e-8 * max(1.0, abs(fd))
 
 
-def _sampled_reference(sp, xyz, cells, p, u_lib, sample, k_user=None):
-    """Oracle values of (A u) at sampled library DoFs, summed over the cells that touch each DoF."""
-    lib_keys = sp.dof_keys()
-    nv = xyz.shape[0]
-    lib_code = encode_keys(lib_keys, nv)
-    order = np.argsort(lib_code)
-    want = set(int(v) for v in np.unique(lib_keys[sample]))
-    touch = np.where(np.isin(cells, list(want)).any(axis=1))[0]
-    keys_t = topology.dof_keys(cells[touch], p)                 # oracle keys of the touching cells
-    code_t = encode_keys(keys_t.reshape(-1, p), nv)
-    lib_of = order[np.searchsorted(lib_code, code_t, sorter=order)].reshape(keys_t.shape[:2])
-    ue = u_lib[lib_of]
-    ye = cg.element_apply(xyz, cells[touch], ue, p, None if k_user is None else k_user[touch])
-    y = np.zeros(sp.n_dofs)
-    np.add.at(y, lib_of.ravel(), ye.ravel())
-    return y[sample]
-
-
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
 def test_config2_full_size_sampled(prec):
     """CG P3 on the 64^3 Kuhn cube (1,572,864 cells, 7,189,057 DoFs), Morton order, the launch the
@@ -163,7 +145,7 @@ def test_config2_full_size_sampled(prec):
     y = to_host(sp.apply(to_dev(u, prec), prec=prec))
     rng = np.random.default_rng(11)
     sample = rng.choice(sp.n_dofs, 512, replace=False)
-    y_ref = _sampled_reference(sp, xyz, cells, p, u, sample)
+    y_ref = sampled_rows(sp, xyz, cells, p, u, sample)
     # the sample's scale: rows of A u are O(h) sums with cancellation; compare against the sampled max
     assert_close(y[sample], y_ref, prec, "config2 sampled")
     # properties that hold at any size
