@@ -10,6 +10,7 @@
 //             wf [nqf], Vf [4][nqf][nd], Ef [4][nqf][3][nd]
 // Structure-of-arrays per tile makes every per-cell load of a warp one
 // coalesced 128-byte (FP32) or 256-byte (FP64) transaction.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -78,6 +79,37 @@ int upload(Ctx& c) {
       }
     }
     if (int s = put(c, &c.d_idx, idx)) return s;
+    // tile-local lists: the tensor-core kernel gathers each distinct DoF of a
+    // tile once and pre-reduces the tile's contributions in shared memory
+    std::vector<int64_t> off(c.ntiles + 1, 0);
+    std::vector<int32_t> list;
+    std::vector<uint16_t> lidx(size_t(c.ntiles) * c.nd * T, 0xFFFF);
+    std::vector<int32_t> buf;
+    list.reserve(size_t(c.nc) * 6);
+    for (int64_t t = 0; t < c.ntiles; ++t) {
+      buf.clear();
+      const int64_t e1 = std::min<int64_t>(c.nc, (t + 1) * T);
+      for (int64_t e = t * T; e < e1; ++e)
+        for (int j = 0; j < c.nd; ++j) {
+          const int32_t d = c.cell_dofs[size_t(e) * c.nd + j];
+          if (!c.mask[d]) buf.push_back(d);
+        }
+      std::sort(buf.begin(), buf.end());
+      buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+      for (int64_t e = t * T; e < e1; ++e)
+        for (int j = 0; j < c.nd; ++j) {
+          const int32_t d = c.cell_dofs[size_t(e) * c.nd + j];
+          if (c.mask[d]) continue;
+          const size_t pos = std::lower_bound(buf.begin(), buf.end(), d) - buf.begin();
+          lidx[(size_t(t) * c.nd + j) * T + (e - t * T)] = uint16_t(pos);
+        }
+      c.tl_max = std::max<int32_t>(c.tl_max, int32_t(buf.size()));
+      list.insert(list.end(), buf.begin(), buf.end());
+      off[t + 1] = int64_t(list.size());
+    }
+    if (int s = put(c, &c.d_tl_off, off)) return s;
+    if (int s = put(c, &c.d_tl_list, list)) return s;
+    if (int s = put(c, &c.d_tl_lidx, lidx)) return s;
     if (c.dirichlet)
       if (int s = put(c, &c.d_mask, c.mask)) return s;
   }

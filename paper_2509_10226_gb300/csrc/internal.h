@@ -67,6 +67,12 @@ struct Ctx {
   int32_t* d_fb_code = nullptr;
   double* d_fb_geo64 = nullptr;
   float* d_fb_geo32 = nullptr;
+  // tile-local DoF lists (CG): distinct unconstrained DoFs of each tile, and
+  // each (cell, local node) as an index into its tile's list (0xFFFF = constrained)
+  int64_t* d_tl_off = nullptr;      // [ntiles + 1]
+  int32_t* d_tl_list = nullptr;     // [d_tl_off[ntiles]]
+  uint16_t* d_tl_lidx = nullptr;    // [ntiles][nd][kTile]
+  int32_t tl_max = 0;               // longest list
   // tensor-core operand images (shared-memory byte images of E^T and E)
   void* d_tc_tf32 = nullptr;
   void* d_tc_bf16 = nullptr;
