@@ -205,6 +205,33 @@ typedef struct {
 int fem_solve(fem_ctx* ctx, const fem_solve_opts* opts, const double* b, double* x,
               fem_solve_stats* stats, void* stream);
 
+/* ---- allocation-free solve ----------------------------------------- */
+
+/* Largest problem fem_solve_noalloc accepts (global DoFs). */
+#define FEM_SOLVE_NOALLOC_MAX_DOFS 262144
+
+/* fem_solve without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not have a library allocate
+ * device memory behind their back, e.g. an application whose memory manager
+ * owns the whole device up front, or a code path that cannot afford the
+ * device-wide synchronisation cudaMalloc/cudaFree may cause.
+ * Same arguments, algorithm, results and errors as fem_solve, except:
+ *   - the work space is a fixed 16 MiB (+64 KiB) device array inside this
+ *     library, reserved on every GPU where the library's device code is
+ *     loaded until the process exits; N > FEM_SOLVE_NOALLOC_MAX_DOFS is
+ *     rejected with FEM_EINVAL before anything runs;
+ *   - the first call on a device looks the array's address up
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device;
+ *   - the calling thread's current device must be the context's device;
+ *   - all calls share the one array and each call overwrites it: calls that
+ *     overlap on the GPU (other streams, threads or contexts) race and must be
+ *     serialised by the caller.
+ * It calls no cudaMalloc, cudaFree, cudaMallocHost or other allocating
+ * routine. */
+int fem_solve_noalloc(fem_ctx* ctx, const fem_solve_opts* opts, const double* b, double* x,
+                      fem_solve_stats* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

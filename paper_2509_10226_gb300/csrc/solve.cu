@@ -16,6 +16,7 @@
 // beta) stay on the device; the host reads one residual norm per iteration.
 #include <chrono>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -207,22 +208,12 @@ int ew_grid(int64_t n) {
   return int(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
-int ensure_work(Ctx& c, Work& w) {
-  const int64_t N = c.ndofs;
-  const size_t need = sizeof(double) * (S_COUNT + 2 * kMaxRedBlocks) + 64 + sizeof(double) * 6 * N +
-                      sizeof(float) * 6 * N + 256 * 16;
-  if (c.work_bytes < need) {
-    void* p = nullptr;
-    TETMF_CK(cudaMalloc(&p, need));
-    c.allocations.push_back(p);
-    c.d_work = p;
-    c.work_bytes = need;
-    TETMF_CK(cudaMemset(p, 0, need));
-  }
-  uint8_t* b = static_cast<uint8_t*>(c.d_work);
+// lay the solver's work arrays out from `base` (nullptr: only measure); returns the bytes used
+size_t carve(uint8_t* base, int64_t N, Work& w) {
+  size_t off = 0;
   auto take = [&](size_t bytes) {
-    uint8_t* r = b;
-    b += (bytes + 255) / 256 * 256;
+    uint8_t* r = base ? base + off : nullptr;
+    off += (bytes + 255) / 256 * 256;
     return r;
   };
   w.scal = reinterpret_cast<double*>(take(sizeof(double) * S_COUNT));
@@ -239,6 +230,21 @@ int ensure_work(Ctx& c, Work& w) {
   w.q = take(sizeof(float) * N);
   w.d = take(sizeof(float) * N);
   w.diag32 = reinterpret_cast<float*>(take(sizeof(float) * N));
+  return off;
+}
+
+int ensure_work(Ctx& c, Work& w) {
+  const int64_t N = c.ndofs;
+  const size_t need = carve(nullptr, N, w);
+  if (c.work_bytes < need) {
+    void* p = nullptr;
+    TETMF_CK(cudaMalloc(&p, need));
+    c.allocations.push_back(p);
+    c.d_work = p;
+    c.work_bytes = need;
+    TETMF_CK(cudaMemset(p, 0, need));
+  }
+  carve(static_cast<uint8_t*>(c.d_work), N, w);
   static thread_local double* pinned = nullptr;
   if (!pinned) TETMF_CK(cudaMallocHost(&pinned, sizeof(double) * S_COUNT));
   w.host_scal = pinned;
@@ -286,11 +292,11 @@ int pcg(Ctx& c, Work& w, Apply apply, T* x, T* r, T* z, T* p, T* q, const T* dia
 
 }  // namespace
 
-int solve(Ctx& c, const fem_solve_opts* o, const double* b, double* x, fem_solve_stats* stats, void* stream) {
+// the solver proper, on work arrays laid out by carve()
+static int solve_with(Ctx& c, Work& w, const fem_solve_opts* o, const double* b, double* x, fem_solve_stats* stats,
+               void* stream) {
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = as_stream(stream);
-  Work w;
-  if (int e = ensure_work(c, w)) return e;
   const int64_t N = c.ndofs;
   const int rg = red_grid(N), eg = ew_grid(N);
   *stats = fem_solve_stats{0, 0, 0.0, 0.0};
@@ -372,4 +378,112 @@ int solve(Ctx& c, const fem_solve_opts* o, const double* b, double* x, fem_solve
   }
 }
 
+int solve(Ctx& c, const fem_solve_opts* o, const double* b, double* x, fem_solve_stats* stats, void* stream) {
+  Work w;
+  if (int e = ensure_work(c, w)) return e;
+  return solve_with(c, w, o, b, x, stats, stream);
+}
+
 }  // namespace tetmf
+
+// ---- allocation-free solve ---------------------------------------------
+//
+// Some callers cannot let a library call cudaMalloc: an application whose
+// memory manager owns all device memory up front (a framework caching
+// allocator, a fixed per-process budget), or one on a path that must not stall,
+// since cudaMalloc/cudaFree can synchronise the device.  fem_solve_noalloc runs
+// the same solver as fem_solve, but its work space (reduction partials and
+// scalars, the FP64 and FP32 PCG vectors) lives in one file-scope device array
+// of a fixed size instead of a buffer the context allocates on first use.
+// That array is reserved on every GPU where this library's device code is
+// loaded, for the life of the process.  Every call shares it: two calls that
+// run on the GPU at the same time (other streams, other threads, other
+// contexts) race on it, so the caller must serialise them.
+
+namespace tetmf {
+namespace {
+
+constexpr int64_t kNoAllocMaxDofs = FEM_SOLVE_NOALLOC_MAX_DOFS;
+constexpr size_t kNoAllocBytes = size_t(kNoAllocMaxDofs) * 64 + (64 << 10);
+static_assert(5 * 8 + 6 * 4 == 64, "per-DoF work bytes");
+
+static __device__ __align__(256) unsigned char g_noalloc_work[kNoAllocBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[64] = {nullptr};
+
+// device address of g_noalloc_work on the current device (looked up once per device)
+int noalloc_address(int dev, void** out) {
+  if (dev < 0 || dev >= 64) {
+    set_error("fem_solve_noalloc: device ordinal %d out of range", dev);
+    return FEM_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_work);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      set_error("fem_solve_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return FEM_ECUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return FEM_OK;
+}
+
+}  // namespace
+}  // namespace tetmf
+
+extern "C" int fem_solve_noalloc(fem_ctx* ctx, const fem_solve_opts* opts, const double* b, double* x,
+                                 fem_solve_stats* stats, void* stream) {
+  using namespace tetmf;
+  if (!ctx || !opts || !b || !x || !stats || (const void*)b == (const void*)x) {
+    set_error("fem_solve_noalloc: null or aliased argument");
+    return FEM_EINVAL;
+  }
+  Ctx& c = ctx->c;
+  if (c.device < 0) {
+    set_error("fem_solve_noalloc: host-only context (device = -1)");
+    return FEM_EINVAL;
+  }
+  if (c.kind != FEM_CG) {
+    set_error("fem_solve_noalloc: CG spaces only");
+    return FEM_EINVAL;
+  }
+  if (opts->mode != FEM_SOLVE_FP64_PCG && opts->mode != FEM_SOLVE_IR_MIXED) {
+    set_error("fem_solve_noalloc: bad mode");
+    return FEM_EINVAL;
+  }
+  if (opts->mode == FEM_SOLVE_IR_MIXED && opts->inner_prec != FEM_FP32 && opts->inner_prec != FEM_TF32 &&
+      opts->inner_prec != FEM_BF16) {
+    set_error("fem_solve_noalloc: inner_prec must be FEM_FP32, FEM_TF32 or FEM_BF16");
+    return FEM_EUNSUPPORTED;
+  }
+  if (!(opts->rtol > 0) || opts->max_inner < 1 || opts->max_outer < 1) {
+    set_error("fem_solve_noalloc: need rtol > 0, max_inner >= 1, max_outer >= 1");
+    return FEM_EINVAL;
+  }
+  Work w;
+  const size_t need = carve(nullptr, c.ndofs, w);
+  if (c.ndofs > kNoAllocMaxDofs || need > kNoAllocBytes) {
+    set_error("fem_solve_noalloc: %lld DoFs exceed the static work space (at most %lld DoFs); use fem_solve",
+              (long long)c.ndofs, (long long)kNoAllocMaxDofs);
+    return FEM_EINVAL;
+  }
+  int dev = -1;
+  TETMF_CK(cudaGetDevice(&dev));
+  if (dev != c.device) {
+    set_error("fem_solve_noalloc: current device %d is not the context's device %d", dev, c.device);
+    return FEM_EINVAL;
+  }
+  void* base = nullptr;
+  if (int e = noalloc_address(dev, &base)) return e;
+  carve(static_cast<uint8_t*>(base), c.ndofs, w);
+  // the reduction ticket must start at zero; every other array is written before it is read
+  TETMF_CK(cudaMemsetAsync(w.ticket, 0, 64, as_stream(stream)));
+  static thread_local double host_scal[S_COUNT];
+  w.host_scal = host_scal;
+  return solve_with(c, w, opts, b, x, stats, stream);
+}

@@ -162,19 +162,24 @@ class FemSpace:
         return y
 
     def solve(self, b, x0=None, mode="ir", inner_prec="fp32", rtol=1e-10, inner_rtol=1e-3, max_outer=50,
-              max_inner=20000, stream=None, raise_on_notconv=True):
-        """Solve A x = b (blocking).  Returns (x, stats dict)."""
+              max_inner=20000, stream=None, raise_on_notconv=True, no_alloc=False):
+        """Solve A x = b (blocking).  Returns (x, stats dict).
+
+        no_alloc=True calls fem_solve_noalloc: the same solver with its work space in
+        the library's fixed device array instead of memory the context allocates (for
+        callers whose device memory must not be allocated by the library; at most
+        FEM_SOLVE_NOALLOC_MAX_DOFS unknowns, concurrent calls must be serialised)."""
         self._check_vec(b, "fp64", "b")
         x = torch.zeros_like(b) if x0 is None else x0.clone()
         opts = _lib.SolveOpts(_lib.FEM_SOLVE_IR_MIXED if mode == "ir" else _lib.FEM_SOLVE_FP64_PCG, PREC[inner_prec],
                               rtol, inner_rtol, max_outer, max_inner)
         st = _lib.SolveStats()
-        status = _lib.lib().fem_solve(self._h, ctypes.byref(opts), _ptr(b), _ptr(x), ctypes.byref(st),
-                                      _stream(stream))
+        fn = _lib.lib().fem_solve_noalloc if no_alloc else _lib.lib().fem_solve
+        status = fn(self._h, ctypes.byref(opts), _ptr(b), _ptr(x), ctypes.byref(st), _stream(stream))
         stats = {"outer": st.outer_iterations, "inner": st.inner_iterations, "rel_residual": st.rel_residual,
                  "seconds": st.seconds, "converged": status == _lib.FEM_OK}
         if status != _lib.FEM_OK and (status != _lib.FEM_ENOTCONV or raise_on_notconv):
-            _lib.check(status, "fem_solve")
+            _lib.check(status, "fem_solve_noalloc" if no_alloc else "fem_solve")
         return x, stats
 
 
