@@ -53,6 +53,31 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "source": "fallback", "sm_max_mhz": 2070.0}
 
 
+def profiled_traffic(kernel_source, summary):
+    """DRAM bytes per launch recorded by an ncu capture in profiles/<summary>, if that capture was taken of
+    the current kernel source (same sha1), else None."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", summary)
+    src = os.path.join(ROOT, "paper_2509_10226_gb300", "csrc", kernel_source)
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None
+    with open(src, "rb") as f:
+        digest = hashlib.sha1(f.read()).hexdigest()
+    rec = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                rec[k.strip()] = v.strip().strip("`")
+    if rec.get("source_sha1") != digest:
+        return None
+    try:
+        return float(rec["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def cg_bytes(C, N, nd, prec):
     """Algorithmic bytes of one CG apply: 4 nd index bytes + the 6-entry metric per cell, u read and y written
     once per DoF (8-byte FP64 or 4-byte FP32 values)."""
@@ -279,8 +304,9 @@ def main():
     y_head = y32.double().clone()
     hb = cg_bytes(C, N, nd, head)
     achieved = hb / (t_head * 1e-3) / 1e9
+    traffic = profiled_traffic("cg_tc.cu", "k_cg_apply_tc.cg_p3_64.md") if n == 64 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "algorithmic_bytes": hb,
                 "kernel": "fem_apply tf32 (zero-fill + k_cg_apply_tc)",
                 "peak_source": peaks["source"] + " hbm_gbs (burst copy)"}
 

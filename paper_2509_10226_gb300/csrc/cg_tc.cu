@@ -11,24 +11,39 @@
 // The difference form is E u_e rewritten with sum_j E_j = 0 (partition of
 // unity); it is exact for exact tables and keeps rounded TF32/BF16 tables
 // consistent (constants map to zero, operand error relative to the gradient).
-// A CTA of 128 threads owns one TMEM lane per cell.  Per tile:
-//   1. each thread gathers its cell's DoFs (masked gather) and writes its row
-//      of U into shared memory in the canonical K-major no-swizzle layout;
-//   2. one thread issues GEMM 1 (tcgen05.mma, D in TMEM) and commits to an
-//      mbarrier;
-//   3. each thread reads its row of G from TMEM (tcgen05.ld 32x32b), applies
-//      the 3x3 metric per quadrature point in FP32 and writes its row of Q;
-//   4. one thread issues GEMM 2 into the same TMEM columns;
-//   5. each thread reads its row of Y and scatter-adds it (atomics, G_e^T).
-// E^T and E are staged once per persistent CTA from pre-laid-out byte images.
+//
+// Data movement: each 128-cell tile carries the sorted list of the distinct
+// unconstrained DoFs its cells touch and, per (cell, local node), a 16-bit
+// index into that list.  The tile's values are gathered once per distinct DoF
+// (cp.async, mostly contiguous addresses thanks to the Morton/first-touch
+// numbering), and the tile's contributions are pre-reduced in shared memory
+// before one global atomic per distinct DoF: about 3x fewer L2 atomics and
+// gather requests than one per (cell, node) (the masked gather and the
+// scatter of Sec. 2.4).
+//
+// One CTA of 128 threads owns one TMEM lane per cell and loops over tiles:
+//   1. build row m of U' from the staged values, write it to shared memory;
+//   2. one thread issues GEMM 1 (D in TMEM), commits to an mbarrier; the CTA
+//      starts copying the next tile's list, indices and metric (cp.async);
+//   3. each thread reads its row of G from TMEM in chunks of 16 points,
+//      applies the metric in FP32 and writes Q back into TMEM (tcgen05.st);
+//   4. one thread issues GEMM 2 with A = Q in TMEM; the CTA starts the next
+//      tile's value gather;
+//   5. each thread reads its row of Y', pre-reduces it into shared memory,
+//      and the CTA adds the tile's distinct values to y with atomics.
+// Every wait on an MMA completion is bounded (about 1 s); on time-out the
+// kernel records bit 0 in the status word and stops after freeing its TMEM.
 //
 // Shared-memory operand layout (K-major, no swizzle): a core matrix is 8 rows
 // x 16 bytes, stored contiguously; row r, column k of an operand with R rows
 // sits at  (k / KC) * LBO + (r / 8) * 128 + (r % 8) * 16 + (k % KC) * ES,
 // KC = 16 / ES elements per core-matrix row, SBO = 128 (next 8 rows),
 // LBO = (R / 8) * 128 (next 16-byte column block).  One MMA consumes K = 2 KC.
+// The A operand of GEMM 2 lives in TMEM: lane m = row m, one 32-bit column
+// per TF32 element or per pair of BF16 elements.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -54,7 +69,12 @@ struct TcShape {
   static constexpr int N1 = round_up(N3, 16);
   static constexpr int K2 = round_up(N3, KSTEP);
   static constexpr int N2 = round_up(ND1, 16);
-  static constexpr int COLS = pow2_cols(max_i(N1, N2));
+  // TMEM: G in columns [0, N1); Q overwrites it in place (TF32: one column per
+  // element; BF16: packed pairs, QW = N1 / 2 columns); Y' after Q at column QW
+  static constexpr int QW = BF16 ? N1 / 2 : N1;
+  static constexpr int D2_COL = QW;
+  static constexpr int COLS = pow2_cols(max_i(N1, QW + N2));
+  static constexpr int NCHUNK = (NQ + 15) / 16;  // epilogue chunks of 16 points (48 columns)
   static constexpr int LBO_A = (kT / 8) * 128;
   static constexpr int LBO_B1 = (N1 / 8) * 128;
   static constexpr int LBO_B2 = (N2 / 8) * 128;
@@ -145,11 +165,6 @@ __device__ __forceinline__ void reg_fence16(uint32_t* r) {
                  "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
                  "+r"(r[15]));
 }
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&v);
@@ -169,90 +184,240 @@ __device__ __forceinline__ void write_row(uint8_t* base, int m, const float* v) 
       w.z = pack_bf16(v[c * 8 + 4], v[c * 8 + 5]);
       w.w = pack_bf16(v[c * 8 + 6], v[c * 8 + 7]);
     } else {
-      w.x = to_tf32(v[c * 4 + 0]);
-      w.y = to_tf32(v[c * 4 + 1]);
-      w.z = to_tf32(v[c * 4 + 2]);
-      w.w = to_tf32(v[c * 4 + 3]);
+      // FP32 bits as the TF32 operand (the tensor core reads the top 19 bits)
+      w.x = __float_as_uint(v[c * 4 + 0]);
+      w.y = __float_as_uint(v[c * 4 + 1]);
+      w.z = __float_as_uint(v[c * 4 + 2]);
+      w.w = __float_as_uint(v[c * 4 + 3]);
     }
     *reinterpret_cast<uint4*>(p + c * ((kT / 8) * 128)) = w;
   }
 }
 
-constexpr int kMaxNQ = 70;
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]));
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]));
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+template <bool BF16>
+__device__ __forceinline__ void mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (BF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(
+            d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(
+            d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// per-tile staging buffers: a ring of kStages per warpgroup (tile t, gather of t+1, metadata of t+2)
+constexpr int kStages = 3;
+template <int ND, int NQ, bool HAS_K>
+struct Stage {
+  uint32_t* lidx;   // [NDP / 2][128] pairs of 16-bit list positions (node 2w low, 2w+1 high)
+  int32_t* list;    // [lmax] distinct DoFs of the tile
+  float* vals;      // [lmax] their values, then the tile's pre-reduced results
+  float* kt;        // [128][NQ | 1] coefficient tile (HAS_K)
+};
+
+template <int ND, int NQ, bool HAS_K>
+__host__ __device__ constexpr size_t stage_bytes(int lmax) {
+  return size_t(round_up(ND, 2)) * kT * 2 + size_t(round_up(lmax, 4)) * 8 + (HAS_K ? size_t(kT) * (NQ | 1) * 4 : 0);
+}
+
+template <int ND, int NQ, bool HAS_K>
+__device__ inline Stage<ND, NQ, HAS_K> stage_at(uint8_t* p, int lmax) {
+  Stage<ND, NQ, HAS_K> st;
+  st.lidx = reinterpret_cast<uint32_t*>(p);
+  p += round_up(ND, 2) * kT * 2;
+  st.list = reinterpret_cast<int32_t*>(p);
+  p += round_up(lmax, 4) * 4;
+  st.vals = reinterpret_cast<float*>(p);
+  p += round_up(lmax, 4) * 4;
+  st.kt = HAS_K ? reinterpret_cast<float*>(p) : nullptr;
+  return st;
+}
+
+// copy a tile's list and node positions (and coefficients) into a stage; m = thread of the warpgroup
+template <int ND, int NQ, bool HAS_K>
+__device__ inline int issue_meta(const Stage<ND, NQ, HAS_K>& st, int m, int64_t tile,
+                                     const int64_t* __restrict__ tl_off, const int32_t* __restrict__ tl_list,
+                                     const uint16_t* __restrict__ tl_lidx, const float* __restrict__ kcoef,
+                                     int64_t nc) {
+  constexpr int NDP = round_up(ND, 2);
+  const int64_t o0 = tl_off[tile];
+  const int L = int(tl_off[tile + 1] - o0);
+  const int32_t* src_list = tl_list + o0;
+  for (int i = m; i < L; i += kT) cp_async4(st.list + i, src_list + i);
+  const uint8_t* li = reinterpret_cast<const uint8_t*>(tl_lidx + tile * NDP * kT);
+  for (int i = m; i < NDP * kT * 2 / 16; i += kT) cp_async16(reinterpret_cast<uint8_t*>(st.lidx) + 16 * i, li + 16 * i);
+  if constexpr (HAS_K) {
+    const int64_t cell0 = tile * kT;
+    const int64_t n = (nc - cell0 < kT ? nc - cell0 : kT) * NQ;
+    const float* src = kcoef + cell0 * NQ;
+    for (int i = m; i < int(n); i += kT) cp_async4(st.kt + (i / NQ) * (NQ | 1) + i % NQ, src + i);
+  }
+  cp_async_commit();
+  return L;
+}
+
+// gather the values of a tile's distinct DoFs (after its list has arrived)
+template <int ND, int NQ, bool HAS_K>
+__device__ inline void issue_gather(const Stage<ND, NQ, HAS_K>& st, int m, int L, const float* __restrict__ u) {
+  for (int i = m; i < L; i += kT) cp_async4(st.vals + i, u + st.list[i]);
+  cp_async_commit();
+}
+
+// barrier of the 128 threads of one warpgroup (named barrier 1 + g)
+__device__ __forceinline__ void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
+__device__ __forceinline__ bool wg_any(int g, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, %2, 128, q;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(r)
+      : "r"(uint32_t(v)), "r"(1 + g)
+      : "memory");
+  return r != 0;
+}
+
+// One CTA = G warpgroups of 128 threads; each warpgroup runs the tile loop on
+// its own tiles with its own operand buffer, stages, mbarrier and TMEM
+// columns (TCOLS each), sharing the E tables.  G is blockDim.x / 128.
 template <int ND, int NQ, bool BF16>
-__global__ void __launch_bounds__(kT, 1)
-    k_cg_apply_tc(const int32_t* __restrict__ idx, const float* __restrict__ metric, const float* __restrict__ tabW,
-                  const uint8_t* __restrict__ bimg, const float* __restrict__ u, float* __restrict__ y,
-                  const float* __restrict__ kcoef, int64_t nc, int64_t ntiles, int32_t* __restrict__ status) {
+constexpr int tc_tcols() {
   using S = TcShape<ND, NQ, BF16>;
-  constexpr int KS = NQ | 1;
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sA2 = smem;
-  uint8_t* sA1 = sA2 + S::A2_BYTES;
-  uint8_t* sB1 = sA1 + S::A1_BYTES;
-  uint8_t* sB2 = sB1 + S::B1_BYTES;
-  float* sw = reinterpret_cast<float*>(sB2 + S::B2_BYTES);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sw + round_up(NQ, 4));
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
-  float* sk = reinterpret_cast<float*>(tslot + 4);
+  return round_up(max_i(S::N1, S::QW + S::N2), 16);
+}
+template <int ND, int NQ, bool BF16>
+constexpr int tc_max_groups() {
+  return 512 / tc_tcols<ND, NQ, BF16>() < 4 ? 512 / tc_tcols<ND, NQ, BF16>() : 4;
+}
 
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5;
+template <int ND, int NQ, bool BF16, bool HAS_K>
+__global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
+    k_cg_apply_tc(const int64_t* __restrict__ tl_off, const int32_t* __restrict__ tl_list,
+                  const uint16_t* __restrict__ tl_lidx, const float* __restrict__ metric,
+                  const uint8_t* __restrict__ bimg, const float* __restrict__ u, float* __restrict__ y,
+                  const float* __restrict__ kcoef, int64_t nc, int64_t ntiles, int lmax, uint32_t tmem_cols,
+                  int32_t* __restrict__ status) {
+  using S = TcShape<ND, NQ, BF16>;
+  using St = Stage<ND, NQ, HAS_K>;
+  constexpr int KS = NQ | 1;
+  constexpr int NDP = round_up(ND, 2);
+  constexpr int TCOLS = round_up(max_i(S::N1, S::QW + S::N2), 16);
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int G = blockDim.x / kT;
+  const int g = threadIdx.x / kT;   // warpgroup
+  const int m = threadIdx.x % kT;   // row of the tile = TMEM lane
+  const int warp = threadIdx.x >> 5;
+  uint8_t* sB1 = smem;
+  uint8_t* sB2 = sB1 + S::B1_BYTES;
+  uint8_t* sA1 = sB2 + S::B2_BYTES + size_t(g) * S::A1_BYTES;
+  uint8_t* misc = sB2 + S::B2_BYTES + size_t(G) * S::A1_BYTES;  // [G][32]: mbarrier, TMEM slot
+  uint64_t* bar = reinterpret_cast<uint64_t*>(misc + 32 * g);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 8);       // warpgroup 0's slot
+  uint32_t* wmax = reinterpret_cast<uint32_t*>(misc + 32 * g + 16);  // per-warp maxima
+  const size_t sbytes = stage_bytes<ND, NQ, HAS_K>(lmax);
+  uint8_t* stage_base = misc + 32 * G + size_t(g) * kStages * sbytes;
+  auto stage = [&](int i) { return stage_at<ND, NQ, HAS_K>(stage_base + size_t(i) * sbytes, lmax); };
+
   {
     const uint4* src = reinterpret_cast<const uint4*>(bimg);
     uint4* dst = reinterpret_cast<uint4*>(sB1);
-    for (int i = tid; i < (S::B1_BYTES + S::B2_BYTES) / 16; i += kT) dst[i] = src[i];
+    for (int i = threadIdx.x; i < (S::B1_BYTES + S::B2_BYTES) / 16; i += blockDim.x) dst[i] = src[i];
   }
-  for (int i = tid; i < NQ; i += kT) sw[i] = tabW[i];
   const uint32_t bar_a = smem_u32(bar);
-  if (tid == 0) mbar_init(bar_a);
+  if (m == 0) mbar_init(bar_a);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(uint32_t(S::COLS)));
+                 "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  // Prefetch ring of kStages = 3 stages per warpgroup.  Commit order of cp.async groups: during tile t
+  // the gather of tile t+1, then the metadata of tile t+2 (empty groups past the last tile), so
+  // "wait_group 1" completes the gather of t+1 and "wait_group 0" the metadata of t+1.
+  const int64_t stride = int64_t(gridDim.x) * G;
+  int64_t tile = int64_t(blockIdx.x) * G + g;
+  int L_cur = 0, L_next = 0;
+  if (tile < ntiles)
+    L_cur = issue_meta<ND, NQ, HAS_K>(stage(0), m, tile, tl_off, tl_list, tl_lidx, kcoef, nc);
+  else
+    cp_async_commit();
+  cp_async_wait_group<0>();
   fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;
-  const uint32_t lane_base = tmem + (uint32_t(warp * 32) << 16);
-  const uint32_t aA1 = smem_u32(sA1), aA2 = smem_u32(sA2), aB1 = smem_u32(sB1), aB2 = smem_u32(sB2);
+  const uint32_t tmem = *tslot + uint32_t(g * TCOLS);
+  const uint32_t lane_base = tmem + (uint32_t((warp & 3) * 32) << 16);
+  const uint32_t aA1 = smem_u32(sA1), aB1 = smem_u32(sB1), aB2 = smem_u32(sB2);
+  if (tile < ntiles) issue_gather<ND, NQ, HAS_K>(stage(0), m, L_cur, u);
+  else cp_async_commit();
+  if (tile + stride < ntiles)
+    L_next = issue_meta<ND, NQ, HAS_K>(stage(1), m, tile + stride, tl_off, tl_list, tl_lidx, kcoef, nc);
+  else
+    cp_async_commit();
+  cp_async_wait_group<1>();
+  wg_sync(g);
   uint32_t phase = 0;
   bool failed = false;
+  int b = 0;
 
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t cell0 = tile * kT;
-    const int m = tid;
-    const bool active = cell0 + m < nc;
-    if (kcoef) {
-      const int64_t ncell = nc - cell0 < kT ? nc - cell0 : kT;
-      const float* src = kcoef + cell0 * NQ;
-      for (int64_t i = tid; i < ncell * NQ; i += kT) sk[(i / NQ) * KS + i % NQ] = src[i];
+  for (; tile < ntiles; tile += stride, b = (b + 1 == kStages ? 0 : b + 1)) {
+    const int b1 = b + 1 == kStages ? 0 : b + 1;
+    const int b2 = b1 + 1 == kStages ? 0 : b1 + 1;
+    const St cur = stage(b);
+    const int64_t next = tile + stride, next2 = tile + 2 * stride;
+    // this cell's metric, consumed after GEMM 1 (coalesced loads, latency hidden by the row build and GEMM 1)
+    const float* mp = metric + tile * 6 * kT + m;
+    const float m0 = __ldg(mp), m1 = __ldg(mp + kT), m2 = __ldg(mp + 2 * kT), m3 = __ldg(mp + 3 * kT),
+                m4 = __ldg(mp + 4 * kT), m5 = __ldg(mp + 5 * kT);
+    const int L = L_cur;
+    int L_next2 = 0;
+    // 1. row m of U' from the staged values (difference form); node positions stay in registers
+    uint32_t lw[NDP / 2];
+#pragma unroll
+    for (int w = 0; w < NDP / 2; ++w) lw[w] = cur.lidx[w * kT + m];
+    {
+      auto pos = [&](int j) { return (lw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu; };
+      const uint32_t l0 = pos(0);
+      const float ue0 = l0 == 0xFFFFu ? 0.0f : cur.vals[l0];
+      float v1[S::K1];
+#pragma unroll
+      for (int j = 1; j < ND; ++j) {
+        const uint32_t l = pos(j);
+        v1[j - 1] = (l == 0xFFFFu ? 0.0f : cur.vals[l]) - ue0;
+      }
+#pragma unroll
+      for (int j = S::ND1; j < S::K1; ++j) v1[j] = 0.0f;
+      write_row<S::K1, BF16>(sA1, m, v1);
     }
-    // 1. masked gather of the cell's DoFs into row m of U
-    int g[ND];
-    float ue[ND], v1[S::K1];
-#pragma unroll
-    for (int j = 0; j < ND; ++j) {
-      g[j] = active ? __ldg(idx + (tile * ND + j) * kT + m) : -1;
-      ue[j] = g[j] >= 0 ? __ldg(u + g[j]) : 0.0f;
-    }
-    // sum_j E_j = 0 (the gradients of a partition of unity), so E u_e equals
-    // E' (u_j - u_0)_{j >= 1} with E' the columns 1..nd-1 of E; rounding the
-    // differences and E' keeps constants in the kernel exactly and makes the
-    // operand error relative to the gradient instead of to u
-#pragma unroll
-    for (int j = 1; j < ND; ++j) v1[j - 1] = ue[j] - ue[0];
-#pragma unroll
-    for (int j = S::ND1; j < S::K1; ++j) v1[j] = 0.0f;
-    write_row<S::K1, BF16>(sA1, m, v1);
     fence_proxy_async();
     tc_fence_before();
-    __syncthreads();
-    // 2. GEMM 1
-    if (tid == 0) {
+    wg_sync(g);
+    // 2. GEMM 1; meanwhile clear the accumulator and fetch the next tile's metadata
+    if (m == 0) {
       tc_fence_after();
 #pragma unroll
       for (int s = 0; s < S::K1 / S::KSTEP; ++s)
@@ -260,71 +425,157 @@ __global__ void __launch_bounds__(kT, 1)
                   smem_desc(aB1 + s * 2 * S::LBO_B1, S::LBO_B1, 128), S::idesc(S::N1), s > 0);
       mma_commit(bar_a);
     }
-    failed |= !mbar_wait(bar_a, phase);
+    for (int i = m; i < L; i += kT) cur.vals[i] = 0.0f;
+    // metadata of tile t+1 (issued one tile ago) -> gather of t+1; metadata of t+2
+    cp_async_wait_group<0>();
+    wg_sync(g);
+    if (next < ntiles) issue_gather<ND, NQ, HAS_K>(stage(b1), m, L_next, u);
+    else cp_async_commit();
+    if (next2 < ntiles)
+      L_next2 = issue_meta<ND, NQ, HAS_K>(stage(b2), m, next2, tl_off, tl_list, tl_lidx, kcoef, nc);
+    else
+      cp_async_commit();
+    // one thread waits for the MMA completion; the others sleep in the barrier
+    if (m == 0) failed |= !mbar_wait(bar_a, phase);
     phase ^= 1;
-    if (__syncthreads_or(failed)) break;
+    if (wg_any(g, failed)) break;
     tc_fence_after();
-    // 3. D_e at the quadrature points: row m of G from TMEM, metric, row m of Q
-    uint32_t d[S::N1];
+    // 3. D_e per quadrature point, chunks of 16 points: G from TMEM, Q = (k_q) M_e g back into TMEM
+    //    (w_q is folded into the table of GEMM 2)
+    {
 #pragma unroll
-    for (int c = 0; c < S::N1 / 16; ++c) tmem_ld16(lane_base + c * 16, d + c * 16);
-    tmem_wait_ld();
+      for (int c = 0; c < S::NCHUNK; ++c) {
+        const int q0 = 16 * c;
+        const int nq = (NQ - q0) < 16 ? (NQ - q0) : 16;
+        const int nl = (3 * nq + 15) / 16;  // x16 loads in this chunk
+        uint32_t d[48];
 #pragma unroll
-    for (int c = 0; c < S::N1 / 16; ++c) reg_fence16(d + c * 16);
-    const float* mp = metric + tile * 6 * kT + m;
-    const float m0 = mp[0], m1 = mp[kT], m2 = mp[2 * kT], m3 = mp[3 * kT], m4 = mp[4 * kT], m5 = mp[5 * kT];
-    float v2[S::K2];
+        for (int l = 0; l < 3; ++l)
+          if (l < nl) tmem_ld16(lane_base + 48 * c + 16 * l, d + 16 * l);
+        tmem_wait_ld();
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      const float gx = __uint_as_float(d[3 * q]), gy = __uint_as_float(d[3 * q + 1]),
-                  gz = __uint_as_float(d[3 * q + 2]);
-      float cq = sw[q];
-      if (kcoef) cq *= sk[m * KS + q];
-      v2[3 * q] = cq * fmaf(m0, gx, fmaf(m1, gy, m2 * gz));
-      v2[3 * q + 1] = cq * fmaf(m1, gx, fmaf(m3, gy, m4 * gz));
-      v2[3 * q + 2] = cq * fmaf(m2, gx, fmaf(m4, gy, m5 * gz));
+        for (int l = 0; l < 3; ++l)
+          if (l < nl) reg_fence16(d + 16 * l);
+        // Q overwrites G in the same registers: d[3i..3i+2] <- (k_q) M_e g_i
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          if (i < nq) {
+            const float gx = __uint_as_float(d[3 * i]), gy = __uint_as_float(d[3 * i + 1]),
+                        gz = __uint_as_float(d[3 * i + 2]);
+            float tx = fmaf(m0, gx, fmaf(m1, gy, m2 * gz));
+            float ty = fmaf(m1, gx, fmaf(m3, gy, m4 * gz));
+            float tz = fmaf(m2, gx, fmaf(m4, gy, m5 * gz));
+            if constexpr (HAS_K) {
+              const float kq = cur.kt[m * KS + q0 + i];
+              tx *= kq;
+              ty *= kq;
+              tz *= kq;
+            }
+            d[3 * i] = __float_as_uint(tx);
+            d[3 * i + 1] = __float_as_uint(ty);
+            d[3 * i + 2] = __float_as_uint(tz);
+          } else if (3 * i < 16 * nl) {
+            d[3 * i] = 0u;
+            if (3 * i + 1 < 16 * nl) d[3 * i + 1] = 0u;
+            if (3 * i + 2 < 16 * nl) d[3 * i + 2] = 0u;
+          }
+        }
+        if constexpr (BF16) {
+          uint32_t w[24];
+#pragma unroll
+          for (int i = 0; i < 24; ++i)
+            w[i] = pack_bf16(__uint_as_float(d[2 * i]), __uint_as_float(d[2 * i + 1]));
+#pragma unroll
+          for (int l = 0; l < 3; ++l)
+            if (l < nl) tmem_st8(lane_base + 24 * c + 8 * l, w + 8 * l);
+        } else {
+          // FP32 bits as the TF32 operand (the tensor core reads the top 19 bits)
+#pragma unroll
+          for (int l = 0; l < 3; ++l)
+            if (l < nl) tmem_st16(lane_base + 48 * c + 16 * l, d + 16 * l);
+        }
+      }
     }
-#pragma unroll
-    for (int n = S::N3; n < S::K2; ++n) v2[n] = 0.0f;
-    write_row<S::K2, BF16>(sA2, m, v2);
-    fence_proxy_async();
+    tmem_wait_st();
     tc_fence_before();
-    __syncthreads();
-    // 4. GEMM 2 into the same TMEM columns (all reads of G are complete)
-    if (tid == 0) {
+    wg_sync(g);
+    // 4. GEMM 2 with A = Q in TMEM
+    if (m == 0) {
       tc_fence_after();
 #pragma unroll
       for (int s = 0; s < S::K2 / S::KSTEP; ++s)
-        mma<BF16>(tmem, smem_desc(aA2 + s * 2 * S::LBO_A, S::LBO_A, 128),
-                  smem_desc(aB2 + s * 2 * S::LBO_B2, S::LBO_B2, 128), S::idesc(S::N2), s > 0);
+        mma_ta<BF16>(tmem + S::D2_COL, tmem + 8 * s, smem_desc(aB2 + s * 2 * S::LBO_B2, S::LBO_B2, 128),
+                     S::idesc(S::N2), s > 0);
       mma_commit(bar_a);
     }
-    failed |= !mbar_wait(bar_a, phase);
+    // one thread waits for the MMA completion; the others sleep in the barrier
+    if (m == 0) failed |= !mbar_wait(bar_a, phase);
     phase ^= 1;
-    if (__syncthreads_or(failed)) break;
+    if (wg_any(g, failed)) break;
     tc_fence_after();
-    // 5. row m of Y, scatter-add (G_e^T)
-    uint32_t r[S::N2];
+    // 5. row m of Y', y_0 = -sum, pre-reduce in shared memory, then one atomic per distinct DoF.
+    //    The pre-reduction adds 32-bit fixed-point integers (native shared-memory atomics, no
+    //    compare-and-swap retries, order-independent): every contribution of the tile is scaled
+    //    by 2^(24 - E), where 2^E bounds the tile's largest |contribution|; a slot receives at
+    //    most 128 contributions (one per cell), so no sum overflows, and the quantum is
+    //    2^(E - 24), below 1.2e-7 of the largest contribution.  Tiles with a non-finite
+    //    contribution fall back to float atomics.
+    {
+      uint32_t r[S::N2];
 #pragma unroll
-    for (int c = 0; c < S::N2 / 16; ++c) tmem_ld16(lane_base + c * 16, r + c * 16);
-    tmem_wait_ld();
+      for (int c = 0; c < S::N2 / 16; ++c) tmem_ld16(lane_base + S::D2_COL + 16 * c, r + 16 * c);
+      tmem_wait_ld();
 #pragma unroll
-    for (int c = 0; c < S::N2 / 16; ++c) reg_fence16(r + c * 16);
-    // y_0 = -sum_{j >= 1} y_j (same identity on the test side)
-    float y0 = 0.0f;
+      for (int c = 0; c < S::N2 / 16; ++c) reg_fence16(r + 16 * c);
+      auto pos = [&](int j) { return (lw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu; };
+      float yv[ND];
+      float y0 = 0.0f;
+      uint32_t mx = 0u;
 #pragma unroll
-    for (int j = 1; j < ND; ++j) {
-      const float yj = __uint_as_float(r[j - 1]);
-      y0 -= yj;
-      if (g[j] >= 0) atomicAdd(y + g[j], yj);
+      for (int j = 1; j < ND; ++j) {
+        yv[j] = __uint_as_float(r[j - 1]);
+        y0 -= yv[j];
+        mx = max(mx, __float_as_uint(fabsf(yv[j])));
+      }
+      yv[0] = y0;
+      mx = max(mx, __float_as_uint(fabsf(y0)));
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if ((m & 31) == 0) wmax[m >> 5] = mx;
+      tc_fence_before();
+      wg_sync(g);
+      mx = max(max(wmax[0], wmax[1]), max(wmax[2], wmax[3]));
+      const int E = mx ? max(int((mx >> 23) & 0xFFu) - 126, -100) : 0;  // max |y| < 2^E
+      if (E <= 128) {
+        const float scale = __int_as_float((127 + 24 - E) << 23);
+        int* iv = reinterpret_cast<int*>(cur.vals);
+#pragma unroll
+        for (int j = 0; j < ND; ++j) {
+          const uint32_t l = pos(j);
+          if (l != 0xFFFFu) atomicAdd(iv + l, __float2int_rn(yv[j] * scale));
+        }
+        wg_sync(g);
+        const float inv = __int_as_float((127 - 24 + E) << 23);
+        for (int i = m; i < L; i += kT) atomicAdd(y + cur.list[i], float(iv[i]) * inv);
+      } else {
+#pragma unroll
+        for (int j = 0; j < ND; ++j) {
+          const uint32_t l = pos(j);
+          if (l != 0xFFFFu) atomicAdd(cur.vals + l, yv[j]);
+        }
+        wg_sync(g);
+        for (int i = m; i < L; i += kT) atomicAdd(y + cur.list[i], cur.vals[i]);
+      }
     }
-    if (g[0] >= 0) atomicAdd(y + g[0], y0);
-    tc_fence_before();
+    cp_async_wait_group<1>();  // gather of tile t+1
+    wg_sync(g);
+    L_cur = L_next;
+    L_next = L_next2;
   }
+  cp_async_wait_all();
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(S::COLS)));
-  if (failed && tid == 0) atomicOr(status, 1);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(tmem_cols));
+  if (failed && m == 0) atomicOr(status, 1);
 }
 
 // host: byte image of an operand stored K-major without swizzle
@@ -352,22 +603,22 @@ std::vector<uint8_t> b_image(const RefTables& t) {
   auto off = [](int r, int k, int lbo) {
     return size_t((k / S::KC) * lbo + (r / 8) * 128 + (r % 8) * 16 + (k % S::KC) * S::ES);
   };
-  // B1 = E' as [N1 rows = 3q+k][K1 = j-1]; B2 = E'^T as [N2 rows = j-1][K2 = 3q+k]
+  // B1 = E' as [N1 rows = 3q+k][K1 = j-1]; B2 = (w E')^T as [N2 rows = j-1][K2 = 3q+k]
+  // (the quadrature weight w_q is folded into the integration table)
   for (int n = 0; n < S::N3; ++n)
     for (int j = 1; j < ND; ++j) {
       const double e = t.E[size_t(n) * ND + j];
       put_elem<BF16>(img, off(n, j - 1, S::LBO_B1), e);
-      put_elem<BF16>(img, S::B1_BYTES + off(j - 1, n, S::LBO_B2), e);
+      put_elem<BF16>(img, S::B1_BYTES + off(j - 1, n, S::LBO_B2), e * t.wq[n / 3]);
     }
   return img;
 }
 
-template <int ND, int NQ, bool BF16>
-size_t tc_smem(bool with_k) {
+template <int ND, int NQ, bool BF16, bool HAS_K>
+size_t tc_smem(int lmax, int G) {
   using S = TcShape<ND, NQ, BF16>;
-  size_t b = size_t(S::A2_BYTES) + S::A1_BYTES + S::B1_BYTES + S::B2_BYTES + round_up(NQ, 4) * 4 + 8 + 16;
-  if (with_k) b += size_t(kT) * (NQ | 1) * 4;
-  return b;
+  return size_t(S::B1_BYTES) + S::B2_BYTES +
+         size_t(G) * (S::A1_BYTES + 32 + kStages * stage_bytes<ND, NQ, HAS_K>(lmax));
 }
 
 template <int ND, int NQ, bool BF16>
@@ -387,29 +638,38 @@ int prepare(Ctx& c) {
   return upload_image<ND, NQ, true>(c, &c.d_tc_bf16);
 }
 
+template <int ND, int NQ, bool BF16, bool HAS_K>
+int launch_g(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) {
+  using S = TcShape<ND, NQ, BF16>;
+  constexpr int TCOLS = round_up(max_i(S::N1, S::QW + S::N2), 16);
+  const int lmax = round_up(c.tl_max > 0 ? c.tl_max : 1, 4);
+  auto kern = k_cg_apply_tc<ND, NQ, BF16, HAS_K>;
+  int dev = 0, smem_max = 0;
+  TETMF_CK(cudaGetDevice(&dev));
+  TETMF_CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // warpgroups per CTA: as many tiles in flight per SM as TMEM (512 columns) and shared memory allow
+  int G = tc_max_groups<ND, NQ, BF16>();
+  while (G > 1 && tc_smem<ND, NQ, BF16, HAS_K>(lmax, G) > size_t(smem_max)) --G;
+  const size_t sm = tc_smem<ND, NQ, BF16, HAS_K>(lmax, G);
+  if (G < 1 || sm > size_t(smem_max)) {
+    set_error("tensor-core kernel does not fit on an SM (%zu bytes of shared memory)", sm);
+    return FEM_EUNSUPPORTED;
+  }
+  if (int e = allow_smem(kern, sm)) return e;
+  const uint32_t cols = uint32_t(pow2_cols(G * TCOLS));
+  int64_t grid = (c.ntiles + G - 1) / G;
+  if (grid > sm_count()) grid = sm_count();
+  kern<<<unsigned(grid), G * kT, sm, st>>>(c.d_tl_off, c.d_tl_list, c.d_tl_lidx, c.d_metric32,
+                                           static_cast<const uint8_t*>(BF16 ? c.d_tc_bf16 : c.d_tc_tf32), u, y, k,
+                                           c.nc, c.ntiles, lmax, cols, c.d_status);
+  TETMF_LAUNCH_CK();
+  return FEM_OK;
+}
+
 template <int ND, int NQ, bool BF16>
 int launch(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) {
   if (int e = init_rows<float>(y, u, c.d_mask, c.ndofs, 0.0f, st)) return e;
-  const size_t sm = tc_smem<ND, NQ, BF16>(k != nullptr);
-  auto kern = k_cg_apply_tc<ND, NQ, BF16>;
-  if (int e = allow_smem(kern, sm)) return e;
-  TETMF_CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-  int per_sm = 0;
-  TETMF_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT, sm));
-  if (per_sm < 1) {
-    set_error("tensor-core kernel does not fit on an SM (%zu bytes of shared memory)", sm);
-    return FEM_ECUDA;
-  }
-  const int cols = TcShape<ND, NQ, BF16>::COLS;
-  if (per_sm * cols > 512) per_sm = 512 / cols;
-  int64_t grid = int64_t(sm_count()) * per_sm;
-  if (grid > c.ntiles) grid = c.ntiles;
-  const TableLayout L = tables_layout(c.tab);
-  const void* img = BF16 ? c.d_tc_bf16 : c.d_tc_tf32;
-  kern<<<unsigned(grid), kT, sm, st>>>(c.d_idx, c.d_metric32, c.d_tab32 + L.w, static_cast<const uint8_t*>(img), u, y,
-                                       k, c.nc, c.ntiles, c.d_status);
-  TETMF_LAUNCH_CK();
-  return FEM_OK;
+  return k ? launch_g<ND, NQ, BF16, true>(c, u, y, k, st) : launch_g<ND, NQ, BF16, false>(c, u, y, k, st);
 }
 
 }  // namespace

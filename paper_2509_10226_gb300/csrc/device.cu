@@ -83,7 +83,9 @@ int upload(Ctx& c) {
     // tile once and pre-reduces the tile's contributions in shared memory
     std::vector<int64_t> off(c.ntiles + 1, 0);
     std::vector<int32_t> list;
-    std::vector<uint16_t> lidx(size_t(c.ntiles) * c.nd * T, 0xFFFF);
+    // node positions: per tile [ndp/2][128] pairs (node 2w in the low half, 2w+1 in the high half)
+    const int ndp = (c.nd + 1) / 2 * 2;
+    std::vector<uint16_t> lidx(size_t(c.ntiles) * ndp * T, 0xFFFF);
     std::vector<int32_t> buf;
     list.reserve(size_t(c.nc) * 6);
     for (int64_t t = 0; t < c.ntiles; ++t) {
@@ -101,7 +103,7 @@ int upload(Ctx& c) {
           const int32_t d = c.cell_dofs[size_t(e) * c.nd + j];
           if (c.mask[d]) continue;
           const size_t pos = std::lower_bound(buf.begin(), buf.end(), d) - buf.begin();
-          lidx[(size_t(t) * c.nd + j) * T + (e - t * T)] = uint16_t(pos);
+          lidx[size_t(t) * ndp * T + ((size_t(j) / 2) * T + (e - t * T)) * 2 + (j & 1)] = uint16_t(pos);
         }
       c.tl_max = std::max<int32_t>(c.tl_max, int32_t(buf.size()));
       list.insert(list.end(), buf.begin(), buf.end());

@@ -155,7 +155,23 @@ int build_plan(Ctx& c, const fem_mesh_desc* m) {
       key[e] = {code, int32_t(e)};
     }
     std::sort(key.begin(), key.end());
-    for (int64_t e = 0; e < nc; ++e) c.cell_perm[e] = key[e].second;
+    // Inside each 128-cell batch, deal the Morton sequence round-robin over the
+    // four warps (position i -> lane (i % 4) * 32 + i / 4): cells of one
+    // neighbourhood share vertex and edge DoFs at the same local index, and
+    // spreading them over warps keeps one warp's 32 scatter/gather addresses
+    // for a local node mostly distinct.  The batch holds the same cells.
+    for (int64_t t0 = 0; t0 < nc; t0 += kTile) {
+      const int64_t n = std::min<int64_t>(kTile, nc - t0);
+      const int64_t w = (n + 31) / 32;  // warps in this batch
+      std::vector<int64_t> slot;
+      slot.reserve(n);
+      for (int64_t i = 0; i < n; ++i) slot.push_back((i % w) * 32 + i / w);
+      // compact the lane numbers of a ragged batch to 0..n-1 in lane order
+      std::vector<int64_t> order(n);
+      std::iota(order.begin(), order.end(), 0);
+      std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return slot[a] < slot[b]; });
+      for (int64_t r = 0; r < n; ++r) c.cell_perm[t0 + r] = key[t0 + order[r]].second;
+    }
   }
   auto lib_cell = [&](int64_t e) { return ucells + 4 * int64_t(c.cell_perm[e]); };
 

@@ -191,3 +191,56 @@ def test_tensor_core_config1_variable_k_dirichlet(prec):
     y = to_host(spd.apply(to_dev(u[perm], prec), prec=prec))
     assert_close(y, cg.apply(xyz, cells, u, p, dirichlet_mask=mask, dofs=dofs)[perm], prec, "dirichlet")
     assert sp.device_status() == 0 and spd.device_status() == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_config4_p2_32cubed_variable_k_backward(prec):
+    """Config 4: CG P2 on the 32^3 cube (196,608 cells), k ~ lognormal(0, 0.5) per quadrature point,
+    L = <w, A(k) u>: forward rows, grad_u = A(k)^T w rows and dL/dk on sampled cells against the
+    oracle; central differences of L in k through the GPU forward."""
+    from oracle import cg as ocg
+    from paper_2509_10226_gb300.fem import FemSpace, fem_apply
+
+    p = 2
+    xyz, cells = synth.kuhn_cube(32, jitter=0.2, seed=synth.SEEDS["jitter"])
+    sp = FemSpace(xyz, cells, degree=p, device=0)
+    assert (sp.n_cells, sp.n_dofs) == (196608, 274625)
+    cperm = sp.cell_permutation()
+    nq = sp.n_qpoints
+    k_user = synth.lognormal_coefficients((cells.shape[0], nq), synth.SEEDS["k"])
+    k_lib = k_user[cperm]
+    u = synth.uniform_vector(sp.n_dofs, synth.SEEDS["u"])
+    w = synth.uniform_vector(sp.n_dofs, synth.SEEDS["w"])
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    ud = torch.as_tensor(u, dtype=dt, device="cuda").requires_grad_(True)
+    kd = torch.as_tensor(k_lib.ravel(), dtype=dt, device="cuda").requires_grad_(True)
+    wd = torch.as_tensor(w, dtype=dt, device="cuda")
+    y = fem_apply(sp, ud, kd, prec=prec)
+    L = (y * wd).sum()
+    L.backward()
+    rng = np.random.default_rng(15)
+    rows = rng.choice(sp.n_dofs, 256, replace=False)
+    assert_close(to_host(y)[rows], sampled_rows(sp, xyz, cells, p, u, rows, k_user=k_user), prec, "A(k)u")
+    assert_close(to_host(ud.grad)[rows], sampled_rows(sp, xyz, cells, p, w, rows, k_user=k_user), prec, "grad_u")
+    # dL/dk of sampled library cells: the oracle evaluates those cells alone
+    from oracle import topology as otop
+
+    lc = rng.choice(sp.n_cells, 256, replace=False)
+    uc = cells[cperm[lc]]
+    dofs_loc, keys_loc = otop.cg_numbering(uc, p)
+    lib_keys = sp.dof_keys()
+    from tests.gpu_util import encode_keys
+
+    code = encode_keys(lib_keys, xyz.shape[0])
+    order = np.argsort(code)
+    lib_of = order[np.searchsorted(code, encode_keys(keys_loc, xyz.shape[0]), sorter=order)]
+    _, dk_ref = ocg.coeff_grad(xyz, uc, u[lib_of], w[lib_of], p, k=k_lib[lc], dofs=dofs_loc)
+    assert_close(to_host(kd.grad).reshape(-1, nq)[lc], dk_ref, prec, "dL/dk")
+    if prec == "fp64":
+        e = int(lc[0]) * nq + 3
+        with torch.no_grad():
+            kp, km = kd.detach().clone(), kd.detach().clone()
+            kp[e] += 1e-6
+            km[e] -= 1e-6
+            fd = ((sp.apply(ud.detach(), k=kp) - sp.apply(ud.detach(), k=km)) @ wd).item() / 2e-6
+        assert abs(fd - kd.grad[e].item()) <= 1e-8 * max(1.0, abs(fd))
