@@ -286,6 +286,7 @@ __device__ inline int issue_meta(const Stage<ND, NQ, HAS_K>& st, int m, int64_t 
 template <int ND, int NQ, bool HAS_K>
 __device__ inline void issue_gather(const Stage<ND, NQ, HAS_K>& st, int m, int L, const float* __restrict__ u) {
   for (int i = m; i < L; i += kT) cp_async4(st.vals + i, u + st.list[i]);
+  if (m == 0) st.vals[L] = 0.0f;  // slot of constrained / padding nodes
   cp_async_commit();
 }
 
@@ -402,12 +403,12 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
     {
       auto pos = [&](int j) { return (lw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu; };
       const uint32_t l0 = pos(0);
-      const float ue0 = l0 == 0xFFFFu ? 0.0f : cur.vals[l0];
+      const float ue0 = cur.vals[l0];
       float v1[S::K1];
 #pragma unroll
       for (int j = 1; j < ND; ++j) {
         const uint32_t l = pos(j);
-        v1[j - 1] = (l == 0xFFFFu ? 0.0f : cur.vals[l]) - ue0;
+        v1[j - 1] = cur.vals[l] - ue0;
       }
 #pragma unroll
       for (int j = S::ND1; j < S::K1; ++j) v1[j] = 0.0f;
@@ -425,21 +426,21 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
                   smem_desc(aB1 + s * 2 * S::LBO_B1, S::LBO_B1, 128), S::idesc(S::N1), s > 0);
       mma_commit(bar_a);
     }
-    for (int i = m; i < L; i += kT) cur.vals[i] = 0.0f;
-    // metadata of tile t+1 (issued one tile ago) -> gather of t+1; metadata of t+2
-    cp_async_wait_group<0>();
-    wg_sync(g);
+    for (int i = m; i <= L; i += kT) cur.vals[i] = 0.0f;
+    cp_async_wait_group<0>();  // this thread's share of the metadata of tile t+1 (issued one tile ago)
+    // one thread waits for the MMA completion; the others sleep in the barrier, which also
+    // publishes the metadata of tile t+1
+    if (m == 0) failed |= !mbar_wait(bar_a, phase);
+    phase ^= 1;
+    if (wg_any(g, failed)) break;
+    tc_fence_after();
+    // gather of tile t+1, metadata of tile t+2
     if (next < ntiles) issue_gather<ND, NQ, HAS_K>(stage(b1), m, L_next, u);
     else cp_async_commit();
     if (next2 < ntiles)
       L_next2 = issue_meta<ND, NQ, HAS_K>(stage(b2), m, next2, tl_off, tl_list, tl_lidx, kcoef, nc);
     else
       cp_async_commit();
-    // one thread waits for the MMA completion; the others sleep in the barrier
-    if (m == 0) failed |= !mbar_wait(bar_a, phase);
-    phase ^= 1;
-    if (wg_any(g, failed)) break;
-    tc_fence_after();
     // 3. D_e per quadrature point, chunks of 16 points: G from TMEM, Q = (k_q) M_e g back into TMEM
     //    (w_q is folded into the table of GEMM 2)
     {
@@ -551,7 +552,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
 #pragma unroll
         for (int j = 0; j < ND; ++j) {
           const uint32_t l = pos(j);
-          if (l != 0xFFFFu) atomicAdd(iv + l, __float2int_rn(yv[j] * scale));
+          atomicAdd(iv + l, __float2int_rn(yv[j] * scale));
         }
         wg_sync(g);
         const float inv = __int_as_float((127 - 24 + E) << 23);
@@ -560,7 +561,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
 #pragma unroll
         for (int j = 0; j < ND; ++j) {
           const uint32_t l = pos(j);
-          if (l != 0xFFFFu) atomicAdd(cur.vals + l, yv[j]);
+          atomicAdd(cur.vals + l, yv[j]);
         }
         wg_sync(g);
         for (int i = m; i < L; i += kT) atomicAdd(y + cur.list[i], cur.vals[i]);
@@ -642,7 +643,7 @@ template <int ND, int NQ, bool BF16, bool HAS_K>
 int launch_g(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) {
   using S = TcShape<ND, NQ, BF16>;
   constexpr int TCOLS = round_up(max_i(S::N1, S::QW + S::N2), 16);
-  const int lmax = round_up(c.tl_max > 0 ? c.tl_max : 1, 4);
+  const int lmax = round_up(c.tl_max + 1, 4);  // list + the zero slot
   auto kern = k_cg_apply_tc<ND, NQ, BF16, HAS_K>;
   int dev = 0, smem_max = 0;
   TETMF_CK(cudaGetDevice(&dev));

@@ -83,9 +83,11 @@ int upload(Ctx& c) {
     // tile once and pre-reduces the tile's contributions in shared memory
     std::vector<int64_t> off(c.ntiles + 1, 0);
     std::vector<int32_t> list;
-    // node positions: per tile [ndp/2][128] pairs (node 2w in the low half, 2w+1 in the high half)
+    // node positions: per tile [ndp/2][128] pairs (node 2w in the low half, 2w+1 in the high half);
+    // constrained nodes, the padding node and the lanes past the last cell point at position L
+    // (one past the list), a slot the kernel keeps at zero on gather and never flushes
     const int ndp = (c.nd + 1) / 2 * 2;
-    std::vector<uint16_t> lidx(size_t(c.ntiles) * ndp * T, 0xFFFF);
+    std::vector<uint16_t> lidx(size_t(c.ntiles) * ndp * T, 0);
     std::vector<int32_t> buf;
     list.reserve(size_t(c.nc) * 6);
     for (int64_t t = 0; t < c.ntiles; ++t) {
@@ -98,6 +100,7 @@ int upload(Ctx& c) {
         }
       std::sort(buf.begin(), buf.end());
       buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+      std::fill(lidx.begin() + size_t(t) * ndp * T, lidx.begin() + size_t(t + 1) * ndp * T, uint16_t(buf.size()));
       for (int64_t e = t * T; e < e1; ++e)
         for (int j = 0; j < c.nd; ++j) {
           const int32_t d = c.cell_dofs[size_t(e) * c.nd + j];
