@@ -70,10 +70,10 @@ struct TcShape {
   static constexpr int K2 = round_up(N3, KSTEP);
   static constexpr int N2 = round_up(ND1, 16);
   // TMEM: G in columns [0, N1); Q overwrites it in place (TF32: one column per
-  // element; BF16: packed pairs, QW = N1 / 2 columns); Y' after Q at column QW
+  // element; BF16: packed pairs, QW = N1 / 2 columns); Y' in [N1, N1 + N2)
   static constexpr int QW = BF16 ? N1 / 2 : N1;
-  static constexpr int D2_COL = QW;
-  static constexpr int COLS = pow2_cols(max_i(N1, QW + N2));
+  static constexpr int D2_COL = N1;  // Y' is read while GEMM 1 of the next tile writes G
+  static constexpr int COLS = pow2_cols(N1 + N2);
   static constexpr int NCHUNK = (NQ + 15) / 16;  // epilogue chunks of 16 points (48 columns)
   static constexpr int LBO_A = (kT / 8) * 128;
   static constexpr int LBO_B1 = (N1 / 8) * 128;
@@ -308,7 +308,7 @@ __device__ __forceinline__ bool wg_any(int g, bool v) {
 template <int ND, int NQ, bool BF16>
 constexpr int tc_tcols() {
   using S = TcShape<ND, NQ, BF16>;
-  return round_up(max_i(S::N1, S::QW + S::N2), 16);
+  return round_up(S::D2_COL + S::N2, 16);
 }
 template <int ND, int NQ, bool BF16>
 constexpr int tc_max_groups() {
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
   using St = Stage<ND, NQ, HAS_K>;
   constexpr int KS = NQ | 1;
   constexpr int NDP = round_up(ND, 2);
-  constexpr int TCOLS = round_up(max_i(S::N1, S::QW + S::N2), 16);
+  constexpr int TCOLS = round_up(S::D2_COL + S::N2, 16);
   extern __shared__ __align__(1024) uint8_t smem[];
   const int G = blockDim.x / kT;
   const int g = threadIdx.x / kT;   // warpgroup
@@ -384,13 +384,67 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
   uint32_t phase = 0;
   bool failed = false;
   int b = 0;
+  // software pipeline across tiles: GEMM 2 of tile t-1 runs while the rows of tile t are built,
+  // GEMM 1 of tile t runs while tile t-1 is scattered and flushed
+  bool have_prev = false;
+  int L_prev = 0;
+  uint32_t lw_prev[NDP / 2];
+#pragma unroll
+  for (int w = 0; w < NDP / 2; ++w) lw_prev[w] = 0u;
+
+  // tile t-1's scatter: row m of Y' from TMEM, y_0 = -sum, fixed-point pre-reduction in shared
+  // memory, then one atomic per distinct DoF.  The pre-reduction adds 32-bit integers (native
+  // shared-memory atomics, no compare-and-swap retries, order-independent): every contribution of
+  // the tile is scaled by 2^(24 - E), where 2^E bounds the tile's largest |contribution|; a slot
+  // receives at most 128 contributions (one per cell), so no sum overflows, and the quantum
+  // 2^(E - 24) is below 1.2e-7 of the largest contribution.  Tiles with a non-finite contribution
+  // fall back to float atomics.
+  auto scatter = [&](const St& st, int Ls, const uint32_t* lwp) {
+    uint32_t r[S::N2];
+#pragma unroll
+    for (int c = 0; c < S::N2 / 16; ++c) tmem_ld16(lane_base + S::D2_COL + 16 * c, r + 16 * c);
+    tmem_wait_ld();
+#pragma unroll
+    for (int c = 0; c < S::N2 / 16; ++c) reg_fence16(r + 16 * c);
+    auto pos = [&](int j) { return (lwp[j >> 1] >> (16 * (j & 1))) & 0xFFFFu; };
+    float yv[ND];
+    float y0 = 0.0f;
+    uint32_t mx = 0u;
+#pragma unroll
+    for (int j = 1; j < ND; ++j) {
+      yv[j] = __uint_as_float(r[j - 1]);
+      y0 -= yv[j];
+      mx = max(mx, __float_as_uint(fabsf(yv[j])));
+    }
+    yv[0] = y0;
+    mx = max(mx, __float_as_uint(fabsf(y0)));
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((m & 31) == 0) wmax[m >> 5] = mx;
+    wg_sync(g);
+    mx = max(max(wmax[0], wmax[1]), max(wmax[2], wmax[3]));
+    const int E = mx ? max(int((mx >> 23) & 0xFFu) - 126, -100) : 0;  // max |y| < 2^E
+    if (E <= 128) {
+      const float scale = __int_as_float((127 + 24 - E) << 23);
+      int* iv = reinterpret_cast<int*>(st.vals);
+#pragma unroll
+      for (int j = 0; j < ND; ++j) atomicAdd(iv + pos(j), __float2int_rn(yv[j] * scale));
+      wg_sync(g);
+      const float inv = __int_as_float((127 - 24 + E) << 23);
+      for (int i = m; i < Ls; i += kT) atomicAdd(y + st.list[i], float(iv[i]) * inv);
+    } else {
+#pragma unroll
+      for (int j = 0; j < ND; ++j) atomicAdd(st.vals + pos(j), yv[j]);
+      wg_sync(g);
+      for (int i = m; i < Ls; i += kT) atomicAdd(y + st.list[i], st.vals[i]);
+    }
+  };
 
   for (; tile < ntiles; tile += stride, b = (b + 1 == kStages ? 0 : b + 1)) {
     const int b1 = b + 1 == kStages ? 0 : b + 1;
-    const int b2 = b1 + 1 == kStages ? 0 : b1 + 1;
+    const int b2 = b1 + 1 == kStages ? 0 : b1 + 1;  // also the stage of tile t-1
     const St cur = stage(b);
     const int64_t next = tile + stride, next2 = tile + 2 * stride;
-    // this cell's metric, consumed after GEMM 1 (coalesced loads, latency hidden by the row build and GEMM 1)
+    // this cell's metric, consumed after GEMM 1 (coalesced loads, latency hidden by the row build)
     const float* mp = metric + tile * 6 * kT + m;
     const float m0 = __ldg(mp), m1 = __ldg(mp + kT), m2 = __ldg(mp + 2 * kT), m3 = __ldg(mp + 3 * kT),
                 m4 = __ldg(mp + 4 * kT), m5 = __ldg(mp + 5 * kT);
@@ -402,24 +456,24 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
     for (int w = 0; w < NDP / 2; ++w) lw[w] = cur.lidx[w * kT + m];
     {
       auto pos = [&](int j) { return (lw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu; };
-      const uint32_t l0 = pos(0);
-      const float ue0 = cur.vals[l0];
+      const float ue0 = cur.vals[pos(0)];
       float v1[S::K1];
 #pragma unroll
-      for (int j = 1; j < ND; ++j) {
-        const uint32_t l = pos(j);
-        v1[j - 1] = cur.vals[l] - ue0;
-      }
+      for (int j = 1; j < ND; ++j) v1[j - 1] = cur.vals[pos(j)] - ue0;
 #pragma unroll
       for (int j = S::ND1; j < S::K1; ++j) v1[j] = 0.0f;
       write_row<S::K1, BF16>(sA1, m, v1);
     }
     fence_proxy_async();
+    // GEMM 2 of tile t-1 must be complete before GEMM 1 of tile t overwrites Q in TMEM
+    if (have_prev && m == 0) failed |= !mbar_wait(bar_a, phase);
+    if (have_prev) phase ^= 1;
     tc_fence_before();
-    wg_sync(g);
-    // 2. GEMM 1; meanwhile clear the accumulator and fetch the next tile's metadata
+    failed = wg_any(g, failed);
+    if (failed) break;
+    tc_fence_after();
+    // 2. GEMM 1 of tile t; meanwhile clear tile t's accumulator and scatter tile t-1
     if (m == 0) {
-      tc_fence_after();
 #pragma unroll
       for (int s = 0; s < S::K1 / S::KSTEP; ++s)
         mma<BF16>(tmem, smem_desc(aA1 + s * 2 * S::LBO_A, S::LBO_A, 128),
@@ -427,12 +481,14 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
       mma_commit(bar_a);
     }
     for (int i = m; i <= L; i += kT) cur.vals[i] = 0.0f;
+    if (have_prev) scatter(stage(b2), L_prev, lw_prev);
     cp_async_wait_group<0>();  // this thread's share of the metadata of tile t+1 (issued one tile ago)
-    // one thread waits for the MMA completion; the others sleep in the barrier, which also
-    // publishes the metadata of tile t+1
+    // one thread waits for GEMM 1; the barrier also publishes the metadata of tile t+1 and the end
+    // of tile t-1's flush (its stage is refilled next)
     if (m == 0) failed |= !mbar_wait(bar_a, phase);
     phase ^= 1;
-    if (wg_any(g, failed)) break;
+    failed = wg_any(g, failed);
+    if (failed) break;
     tc_fence_after();
     // gather of tile t+1, metadata of tile t+2
     if (next < ntiles) issue_gather<ND, NQ, HAS_K>(stage(b1), m, L_next, u);
@@ -500,7 +556,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
     tmem_wait_st();
     tc_fence_before();
     wg_sync(g);
-    // 4. GEMM 2 with A = Q in TMEM
+    // 4. GEMM 2 of tile t (A = Q in TMEM); its completion is awaited before GEMM 1 of tile t+1
     if (m == 0) {
       tc_fence_after();
 #pragma unroll
@@ -509,68 +565,24 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
                      S::idesc(S::N2), s > 0);
       mma_commit(bar_a);
     }
-    // one thread waits for the MMA completion; the others sleep in the barrier
-    if (m == 0) failed |= !mbar_wait(bar_a, phase);
-    phase ^= 1;
-    if (wg_any(g, failed)) break;
-    tc_fence_after();
-    // 5. row m of Y', y_0 = -sum, pre-reduce in shared memory, then one atomic per distinct DoF.
-    //    The pre-reduction adds 32-bit fixed-point integers (native shared-memory atomics, no
-    //    compare-and-swap retries, order-independent): every contribution of the tile is scaled
-    //    by 2^(24 - E), where 2^E bounds the tile's largest |contribution|; a slot receives at
-    //    most 128 contributions (one per cell), so no sum overflows, and the quantum is
-    //    2^(E - 24), below 1.2e-7 of the largest contribution.  Tiles with a non-finite
-    //    contribution fall back to float atomics.
-    {
-      uint32_t r[S::N2];
+    cp_async_wait_group<1>();  // gather of tile t+1 (this thread's share; published by the next barrier)
+    have_prev = true;
+    L_prev = L;
 #pragma unroll
-      for (int c = 0; c < S::N2 / 16; ++c) tmem_ld16(lane_base + S::D2_COL + 16 * c, r + 16 * c);
-      tmem_wait_ld();
-#pragma unroll
-      for (int c = 0; c < S::N2 / 16; ++c) reg_fence16(r + 16 * c);
-      auto pos = [&](int j) { return (lw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu; };
-      float yv[ND];
-      float y0 = 0.0f;
-      uint32_t mx = 0u;
-#pragma unroll
-      for (int j = 1; j < ND; ++j) {
-        yv[j] = __uint_as_float(r[j - 1]);
-        y0 -= yv[j];
-        mx = max(mx, __float_as_uint(fabsf(yv[j])));
-      }
-      yv[0] = y0;
-      mx = max(mx, __float_as_uint(fabsf(y0)));
-      mx = __reduce_max_sync(0xffffffffu, mx);
-      if ((m & 31) == 0) wmax[m >> 5] = mx;
-      tc_fence_before();
-      wg_sync(g);
-      mx = max(max(wmax[0], wmax[1]), max(wmax[2], wmax[3]));
-      const int E = mx ? max(int((mx >> 23) & 0xFFu) - 126, -100) : 0;  // max |y| < 2^E
-      if (E <= 128) {
-        const float scale = __int_as_float((127 + 24 - E) << 23);
-        int* iv = reinterpret_cast<int*>(cur.vals);
-#pragma unroll
-        for (int j = 0; j < ND; ++j) {
-          const uint32_t l = pos(j);
-          atomicAdd(iv + l, __float2int_rn(yv[j] * scale));
-        }
-        wg_sync(g);
-        const float inv = __int_as_float((127 - 24 + E) << 23);
-        for (int i = m; i < L; i += kT) atomicAdd(y + cur.list[i], float(iv[i]) * inv);
-      } else {
-#pragma unroll
-        for (int j = 0; j < ND; ++j) {
-          const uint32_t l = pos(j);
-          atomicAdd(cur.vals + l, yv[j]);
-        }
-        wg_sync(g);
-        for (int i = m; i < L; i += kT) atomicAdd(y + cur.list[i], cur.vals[i]);
-      }
-    }
-    cp_async_wait_group<1>();  // gather of tile t+1
-    wg_sync(g);
+    for (int w = 0; w < NDP / 2; ++w) lw_prev[w] = lw[w];
     L_cur = L_next;
     L_next = L_next2;
+    wg_sync(g);
+  }
+  // the last tile's scatter
+  if (have_prev && !failed) {
+    if (m == 0) failed |= !mbar_wait(bar_a, phase);
+    tc_fence_before();
+    failed = wg_any(g, failed);
+    if (!failed) {
+      tc_fence_after();
+      scatter(stage(b == 0 ? kStages - 1 : b - 1), L_prev, lw_prev);
+    }
   }
   cp_async_wait_all();
   tc_fence_before();
@@ -642,7 +654,7 @@ int prepare(Ctx& c) {
 template <int ND, int NQ, bool BF16, bool HAS_K>
 int launch_g(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) {
   using S = TcShape<ND, NQ, BF16>;
-  constexpr int TCOLS = round_up(max_i(S::N1, S::QW + S::N2), 16);
+  constexpr int TCOLS = round_up(S::D2_COL + S::N2, 16);
   const int lmax = round_up(c.tl_max + 1, 4);  // list + the zero slot
   auto kern = k_cg_apply_tc<ND, NQ, BF16, HAS_K>;
   int dev = 0, smem_max = 0;
