@@ -196,6 +196,28 @@ def oracle_cpu_baseline(xyz, cells, p, N, target_s=10.0):
                       f"{t:.1f} s, scaled by N/C = {N / C:.4f} DoFs per cell"}
 
 
+def time_solves(torch, FemSpace, device):
+    """Poisson solve -Laplace u = 1, homogeneous Dirichlet, CG P3 on the 48^3 cube (3,048,625 DoFs) to a
+    relative residual of 1e-10: FP64 iterative refinement around the TF32 / FP32 inner Jacobi-PCG,
+    against the all-FP64 Jacobi-PCG (wall time of each solve, after one short warm-up solve)."""
+    xyz, cells = synth.kuhn_cube(48, jitter=0.2, seed=synth.SEEDS["jitter"])
+    sp = FemSpace(xyz, cells, kind="cg", degree=3, dirichlet=True, device=device)
+    b = sp.rhs_const(1.0)
+    sp.solve(b, mode="ir", inner_prec="tf32", rtol=1e-3, raise_on_notconv=False)
+    out = {"n_dofs": sp.n_dofs, "rtol": 1e-10}
+    for name, mode, inner in (("ir_tf32", "ir", "tf32"), ("ir_bf16", "ir", "bf16"), ("ir_fp32", "ir", "fp32"),
+                              ("pcg_fp64", "pcg", "fp32")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, st = sp.solve(b, mode=mode, inner_prec=inner, rtol=1e-10, inner_rtol=1e-3, raise_on_notconv=False)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        out[name] = {"seconds": t, "outer": st["outer"], "inner": st["inner"], "rel_residual": st["rel_residual"],
+                     "converged": st["converged"]}
+    out["speedup_ir_tf32_vs_fp64"] = out["pcg_fp64"]["seconds"] / out["ir_tf32"]["seconds"]
+    return out
+
+
 def run_reference(args):
     """--impl reference: the oracle on the host cores, each step a bounded sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -244,6 +266,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="time the headline apply only")
     ap.add_argument("--no-dg", action="store_true")
     ap.add_argument("--no-csr", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -371,6 +394,11 @@ def main():
                                                "rel_l2_vs_fp64": rel(y_), "build_s": build_s}
             except Exception as e:  # noqa: BLE001
                 variants["csr"] = {"unavailable": str(e).splitlines()[0]}
+        if not args.no_solve:
+            try:
+                variants["solve_cg_p3_48"] = time_solves(torch, FemSpace, local)
+            except Exception as e:  # noqa: BLE001
+                variants["solve_cg_p3_48"] = {"unavailable": str(e).splitlines()[0]}
         if not args.no_dg:
             try:
                 xd, cd = synth.kuhn_cube(48, jitter=0.2, seed=synth.SEEDS["jitter"])

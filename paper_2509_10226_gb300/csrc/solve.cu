@@ -25,6 +25,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kMaxRedBlocks = 1024;
+constexpr int kCheck = 8;  // PCG iterations between residual checks on the host
 
 // scalar slots in the solver's device scalar array
 enum : int { S_PQ = 0, S_RZ0 = 1, S_RZ1 = 2, S_RR = 3, S_NORM = 4, S_RES = 5, S_COUNT = 8 };
@@ -169,7 +170,8 @@ __global__ void __launch_bounds__(kBlock) k_pcg_update(T* __restrict__ x, T* __r
                                                        const T* __restrict__ diag, int64_t n, const double* rz,
                                                        const double* pq, double* partials, unsigned* ticket,
                                                        double* rz_next, double* rr) {
-  const T alpha = T(*rz / *pq);
+  const double pqv = *pq;
+  const T alpha = pqv != 0.0 ? T(*rz / pqv) : T(0);
   double a = 0.0, b = 0.0;
   GRID_STRIDE(i, n) {
     x[i] = fma(alpha, p[i], x[i]);
@@ -187,7 +189,8 @@ __global__ void __launch_bounds__(kBlock) k_pcg_update(T* __restrict__ x, T* __r
 template <typename T>
 __global__ void k_pcg_direction(T* __restrict__ p, const T* __restrict__ z, int64_t n, const double* rz_next,
                                 const double* rz) {
-  const T beta = T(*rz_next / *rz);
+  const double rzv = *rz;
+  const T beta = rzv != 0.0 ? T(*rz_next / rzv) : T(0);
   GRID_STRIDE(i, n) p[i] = fma(beta, p[i], z[i]);
 }
 
@@ -281,6 +284,9 @@ int pcg(Ctx& c, Work& w, Apply apply, T* x, T* r, T* z, T* p, T* q, const T* dia
     k_pcg_direction<T><<<eg, kBlock, 0, st>>>(p, z, N, w.scal + nxt, w.scal + cur);
     TETMF_LAUNCH_CK();
     ++iters;
+    // the host reads the residual every kCheck iterations only (one synchronisation); the
+    // iterations run past convergence keep reducing it (a zero denominator yields a zero step)
+    if (iters % kCheck != 0 && iters < max_it) continue;
     if (int e = read_scalar(w.scal + S_RR, w.host_scal, rr, st)) return e;
     if (!std::isfinite(rr)) {
       set_error("fem_solve: residual is not finite after %d iterations", iters);
