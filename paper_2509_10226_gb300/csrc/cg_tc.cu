@@ -262,14 +262,14 @@ __device__ inline Stage<ND, NQ, HAS_K> stage_at(uint8_t* p, int lmax) {
 // copy a tile's list and node positions (and coefficients) into a stage; m = thread of the warpgroup
 template <int ND, int NQ, bool HAS_K>
 __device__ inline int issue_meta(const Stage<ND, NQ, HAS_K>& st, int m, int64_t tile,
-                                     const int64_t* __restrict__ tl_off, const int32_t* __restrict__ tl_list,
+                                     const int64_t* __restrict__ tl_span, const int32_t* __restrict__ tl_list,
                                      const uint16_t* __restrict__ tl_lidx, const float* __restrict__ kcoef,
                                      int64_t nc) {
   constexpr int NDP = round_up(ND, 2);
-  const int64_t o0 = tl_off[tile];
-  const int L = int(tl_off[tile + 1] - o0);
-  const int32_t* src_list = tl_list + o0;
-  for (int i = m; i < L; i += kT) cp_async4(st.list + i, src_list + i);
+  const int64_t o0 = tl_span[2 * tile];
+  const int L = int(tl_span[2 * tile + 1]);
+  const int32_t* src_list = tl_list + o0;  // 16-byte aligned, padded to a multiple of 4 entries
+  for (int i = m; i < (L + 3) / 4; i += kT) cp_async16(st.list + 4 * i, src_list + 4 * i);
   const uint8_t* li = reinterpret_cast<const uint8_t*>(tl_lidx + tile * NDP * kT);
   for (int i = m; i < NDP * kT * 2 / 16; i += kT) cp_async16(reinterpret_cast<uint8_t*>(st.lidx) + 16 * i, li + 16 * i);
   if constexpr (HAS_K) {
@@ -317,7 +317,7 @@ constexpr int tc_max_groups() {
 
 template <int ND, int NQ, bool BF16, bool HAS_K>
 __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
-    k_cg_apply_tc(const int64_t* __restrict__ tl_off, const int32_t* __restrict__ tl_list,
+    k_cg_apply_tc(const int64_t* __restrict__ tl_span, const int32_t* __restrict__ tl_list,
                   const uint16_t* __restrict__ tl_lidx, const float* __restrict__ metric,
                   const uint8_t* __restrict__ bimg, const float* __restrict__ u, float* __restrict__ y,
                   const float* __restrict__ kcoef, int64_t nc, int64_t ntiles, int lmax, uint32_t tmem_cols,
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
   int64_t tile = int64_t(blockIdx.x) * G + g;
   int L_cur = 0, L_next = 0;
   if (tile < ntiles)
-    L_cur = issue_meta<ND, NQ, HAS_K>(stage(0), m, tile, tl_off, tl_list, tl_lidx, kcoef, nc);
+    L_cur = issue_meta<ND, NQ, HAS_K>(stage(0), m, tile, tl_span, tl_list, tl_lidx, kcoef, nc);
   else
     cp_async_commit();
   cp_async_wait_group<0>();
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
   if (tile < ntiles) issue_gather<ND, NQ, HAS_K>(stage(0), m, L_cur, u);
   else cp_async_commit();
   if (tile + stride < ntiles)
-    L_next = issue_meta<ND, NQ, HAS_K>(stage(1), m, tile + stride, tl_off, tl_list, tl_lidx, kcoef, nc);
+    L_next = issue_meta<ND, NQ, HAS_K>(stage(1), m, tile + stride, tl_span, tl_list, tl_lidx, kcoef, nc);
   else
     cp_async_commit();
   cp_async_wait_group<1>();
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
                   smem_desc(aB1 + s * 2 * S::LBO_B1, S::LBO_B1, 128), S::idesc(S::N1), s > 0);
       mma_commit(bar_a);
     }
-    for (int i = m; i <= L; i += kT) cur.vals[i] = 0.0f;
+    for (int i = m; i < (L + 4) / 4; i += kT) reinterpret_cast<float4*>(cur.vals)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (have_prev) scatter(stage(b2), L_prev, lw_prev);
     cp_async_wait_group<0>();  // this thread's share of the metadata of tile t+1 (issued one tile ago)
     // one thread waits for GEMM 1; the barrier also publishes the metadata of tile t+1 and the end
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
     if (next < ntiles) issue_gather<ND, NQ, HAS_K>(stage(b1), m, L_next, u);
     else cp_async_commit();
     if (next2 < ntiles)
-      L_next2 = issue_meta<ND, NQ, HAS_K>(stage(b2), m, next2, tl_off, tl_list, tl_lidx, kcoef, nc);
+      L_next2 = issue_meta<ND, NQ, HAS_K>(stage(b2), m, next2, tl_span, tl_list, tl_lidx, kcoef, nc);
     else
       cp_async_commit();
     // 3. D_e per quadrature point, chunks of 16 points: G from TMEM, Q = (k_q) M_e g back into TMEM
@@ -672,7 +672,7 @@ int launch_g(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) 
   const uint32_t cols = uint32_t(pow2_cols(G * TCOLS));
   int64_t grid = (c.ntiles + G - 1) / G;
   if (grid > sm_count()) grid = sm_count();
-  kern<<<unsigned(grid), G * kT, sm, st>>>(c.d_tl_off, c.d_tl_list, c.d_tl_lidx, c.d_metric32,
+  kern<<<unsigned(grid), G * kT, sm, st>>>(c.d_tl_span, c.d_tl_list, c.d_tl_lidx, c.d_metric32,
                                            static_cast<const uint8_t*>(BF16 ? c.d_tc_bf16 : c.d_tc_tf32), u, y, k,
                                            c.nc, c.ntiles, lmax, cols, c.d_status);
   TETMF_LAUNCH_CK();

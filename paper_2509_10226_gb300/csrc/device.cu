@@ -81,7 +81,7 @@ int upload(Ctx& c) {
     if (int s = put(c, &c.d_idx, idx)) return s;
     // tile-local lists: the tensor-core kernel gathers each distinct DoF of a
     // tile once and pre-reduces the tile's contributions in shared memory
-    std::vector<int64_t> off(c.ntiles + 1, 0);
+    std::vector<int64_t> span(size_t(c.ntiles) * 2, 0);
     std::vector<int32_t> list;
     // node positions: per tile [ndp/2][128] pairs (node 2w in the low half, 2w+1 in the high half);
     // constrained nodes, the padding node and the lanes past the last cell point at position L
@@ -109,10 +109,12 @@ int upload(Ctx& c) {
           lidx[size_t(t) * ndp * T + ((size_t(j) / 2) * T + (e - t * T)) * 2 + (j & 1)] = uint16_t(pos);
         }
       c.tl_max = std::max<int32_t>(c.tl_max, int32_t(buf.size()));
+      span[2 * t] = int64_t(list.size());
+      span[2 * t + 1] = int64_t(buf.size());
       list.insert(list.end(), buf.begin(), buf.end());
-      off[t + 1] = int64_t(list.size());
+      while (list.size() % 4) list.push_back(buf.empty() ? 0 : buf.back());  // 16-byte aligned lists
     }
-    if (int s = put(c, &c.d_tl_off, off)) return s;
+    if (int s = put(c, &c.d_tl_span, span)) return s;
     if (int s = put(c, &c.d_tl_list, list)) return s;
     if (int s = put(c, &c.d_tl_lidx, lidx)) return s;
     if (c.dirichlet)

@@ -69,8 +69,8 @@ struct Ctx {
   float* d_fb_geo32 = nullptr;
   // tile-local DoF lists (CG): distinct unconstrained DoFs of each tile, and
   // each (cell, local node) as an index into its tile's list (0xFFFF = constrained)
-  int64_t* d_tl_off = nullptr;      // [ntiles + 1]
-  int32_t* d_tl_list = nullptr;     // [d_tl_off[ntiles]]
+  int64_t* d_tl_span = nullptr;     // [ntiles][2]: offset (a multiple of 4) and length of the list
+  int32_t* d_tl_list = nullptr;     // lists, each padded to a multiple of 4 entries
   uint16_t* d_tl_lidx = nullptr;    // [ntiles][nd][kTile]
   int32_t tl_max = 0;               // longest list
   // tensor-core operand images (shared-memory byte images of E^T and E)
