@@ -376,7 +376,17 @@ int build_plan(Ctx& c, const fem_mesh_desc* m) {
       }
       fl.push_back({e1, e2, f1, f2, o});
     }
+    // faces in owner order, then inside windows of 4096 faces grouped by (local face of each side,
+    // orientation): a warp of 32 consecutive faces then mostly reads the same reference-table rows
+    // (broadcast) while the window keeps the owner locality
     std::sort(fl.begin(), fl.end(), [](const F& a, const F& b) { return a.cm < b.cm || (a.cm == b.cm && a.fm < b.fm); });
+    for (size_t w0 = 0; w0 < fl.size(); w0 += 4096) {
+      const size_t w1 = std::min(fl.size(), w0 + 4096);
+      std::stable_sort(fl.begin() + w0, fl.begin() + w1, [](const F& a, const F& b) {
+        const int ka = (a.fm * 4 + a.fp) * 6 + a.o, kb = (b.fm * 4 + b.fp) * 6 + b.o;
+        return ka < kb;
+      });
+    }
     c.nfi = int64_t(fl.size());
     c.fi_cell.resize(size_t(2) * c.nfi);
     c.fi_code.resize(c.nfi);
