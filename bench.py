@@ -407,15 +407,18 @@ def main():
                 du32 = du64.float()
                 dy64 = torch.empty_like(du64)
                 dy32 = torch.empty_like(du32)
-                for prec, u_, y_ in (("fp64", du64, dy64), ("fp32", du32, dy32)):
+                dytc = {q: torch.empty_like(du32) for q in ("tf32", "bf16")}
+                for prec, u_, y_ in (("fp64", du64, dy64), ("fp32", du32, dy32), ("tf32", du32, dytc["tf32"]),
+                                     ("bf16", du32, dytc["bf16"])):
                     msv = time_steps(torch, lambda: dsp.apply(u_, prec=prec, out=y_), vsteps, 2, flush, stream,
                                      barrier)
                     t = float(np.mean(msv))
                     b = dg_bytes(dsp.n_cells, dsp.n_interior_faces, dsp.n_boundary_faces, 10, prec)
                     variants[f"dg_p2_48_{prec}"] = {"gdofs": dsp.n_dofs / (t * 1e-3) / 1e9, "ms": t,
                                                     "n_dofs": dsp.n_dofs, "hbm_gbs": b / (t * 1e-3) / 1e9}
-                variants["dg_p2_48_fp32"]["rel_l2_vs_fp64"] = float(
-                    torch.linalg.norm(dy32.double() - dy64) / torch.linalg.norm(dy64))
+                for prec, y_ in (("fp32", dy32), ("tf32", dytc["tf32"]), ("bf16", dytc["bf16"])):
+                    variants[f"dg_p2_48_{prec}"]["rel_l2_vs_fp64"] = float(
+                        torch.linalg.norm(y_.double() - dy64) / torch.linalg.norm(dy64))
                 del dsp
             except Exception as e:  # noqa: BLE001
                 variants["dg_p2_48"] = {"unavailable": str(e).splitlines()[0]}

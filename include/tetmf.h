@@ -151,7 +151,9 @@ int fem_device_status(fem_ctx* ctx, int32_t* status);
 /* y = A(k) u.  u, y: device vectors of N values (double for FEM_FP64, float
  * otherwise), library order, must not alias.  k: NULL (k = 1) or device
  * [n_cells][nq] of the vector type.  Eq. 3 (CG), Eq. 5 (DG).  DG supports
- * FEM_FP64 and FEM_FP32 with k = NULL.  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+ * k = NULL only; its FEM_TF32 / FEM_BF16 path (cell and interior-face products
+ * on the tensor cores, boundary faces in FP32) wants u and y 16-byte aligned
+ * (EINVAL otherwise).  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
 int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k, void* stream);
 
 /* out = A(k)^T g (the transposed chain G^T E^T D^T E G; D_e is symmetric).

@@ -48,188 +48,15 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace tetmf {
 namespace {
 
 constexpr int kT = kTile;
 
-__host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
-__host__ __device__ constexpr int pow2_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512; }
-__host__ __device__ constexpr int max_i(int a, int b) { return a > b ? a : b; }
 
-template <int ND, int NQ, bool BF16>
-struct TcShape {
-  static constexpr int ES = BF16 ? 2 : 4;
-  static constexpr int KC = 16 / ES;
-  static constexpr int KSTEP = 2 * KC;
-  static constexpr int N3 = 3 * NQ;
-  static constexpr int ND1 = ND - 1;  // DoFs 1..nd-1 enter as differences to DoF 0
-  static constexpr int K1 = round_up(ND1, KSTEP);
-  static constexpr int N1 = round_up(N3, 16);
-  static constexpr int K2 = round_up(N3, KSTEP);
-  static constexpr int N2 = round_up(ND1, 16);
-  // TMEM: G in columns [0, N1); Q overwrites it in place (TF32: one column per
-  // element; BF16: packed pairs, QW = N1 / 2 columns); Y' in [N1, N1 + N2)
-  static constexpr int QW = BF16 ? N1 / 2 : N1;
-  static constexpr int D2_COL = N1;  // Y' is read while GEMM 1 of the next tile writes G
-  static constexpr int COLS = pow2_cols(N1 + N2);
-  static constexpr int NCHUNK = (NQ + 15) / 16;  // epilogue chunks of 16 points (48 columns)
-  static constexpr int LBO_A = (kT / 8) * 128;
-  static constexpr int LBO_B1 = (N1 / 8) * 128;
-  static constexpr int LBO_B2 = (N2 / 8) * 128;
-  static constexpr int A1_BYTES = kT * K1 * ES;
-  static constexpr int A2_BYTES = kT * K2 * ES;
-  static constexpr int B1_BYTES = N1 * K1 * ES;
-  static constexpr int B2_BYTES = N2 * K2 * ES;
-  // instruction descriptor (kind::tf32 / kind::f16): D = F32 (bits 4-5 = 1),
-  // A/B format (bits 7-9, 10-12) = TF32 (2) or BF16 (1), both K-major,
-  // N >> 3 at bits 17-22, M >> 4 at bits 24-28
-  static constexpr uint32_t fmt = BF16 ? 1u : 2u;
-  __host__ __device__ static constexpr uint32_t idesc(int n) {
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(kT >> 4) << 24);
-  }
-  static_assert(N1 % 16 == 0 && N1 >= 16 && N1 <= 256, "GEMM 1 N out of range");
-  static_assert(N2 % 16 == 0 && N2 >= 16 && N2 <= 256, "GEMM 2 N out of range");
-};
 
-// ---- PTX wrappers ---------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait: gives up after ~1 s so that a lost completion cannot hang the GPU
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > 1000000000ull) return false;
-  return true;
-}
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  // start >> 4 (bits 0-13), LBO >> 4 (16-29), SBO >> 4 (32-45), version 1 (46-47),
-  // base offset 0, layout SWIZZLE_NONE (61-63 = 0)
-  return uint64_t((addr >> 4) & 0x3FFF) | (uint64_t((lbo >> 4) & 0x3FFF) << 16) |
-         (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
-}
-template <bool BF16>
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if constexpr (BF16) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
-            d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
-            d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  }
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-      "[%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-// keeps every use of the loaded registers after tcgen05.wait::ld
-__device__ __forceinline__ void reg_fence16(uint32_t* r) {
-  asm volatile(""
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                 "+r"(r[15]));
-}
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-// write one K-major row (row m) of K values into an operand with LBO = LBO_A
-template <int K, bool BF16>
-__device__ __forceinline__ void write_row(uint8_t* base, int m, const float* v) {
-  constexpr int KC = BF16 ? 8 : 4;
-  uint8_t* p = base + (m / 8) * 128 + (m % 8) * 16;
-#pragma unroll
-  for (int c = 0; c < K / KC; ++c) {
-    uint4 w;
-    if constexpr (BF16) {
-      w.x = pack_bf16(v[c * 8 + 0], v[c * 8 + 1]);
-      w.y = pack_bf16(v[c * 8 + 2], v[c * 8 + 3]);
-      w.z = pack_bf16(v[c * 8 + 4], v[c * 8 + 5]);
-      w.w = pack_bf16(v[c * 8 + 6], v[c * 8 + 7]);
-    } else {
-      // FP32 bits as the TF32 operand (the tensor core reads the top 19 bits)
-      w.x = __float_as_uint(v[c * 4 + 0]);
-      w.y = __float_as_uint(v[c * 4 + 1]);
-      w.z = __float_as_uint(v[c * 4 + 2]);
-      w.w = __float_as_uint(v[c * 4 + 3]);
-    }
-    *reinterpret_cast<uint4*>(p + c * ((kT / 8) * 128)) = w;
-  }
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16};" ::"r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
-      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]));
-}
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(r[0]),
-               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]));
-}
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-template <bool BF16>
-__device__ __forceinline__ void mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if constexpr (BF16) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(
-            d_tmem),
-        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(
-            d_tmem),
-        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
-  }
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // per-tile staging buffers: a ring of kStages per warpgroup (tile t, gather of t+1, metadata of t+2)
 constexpr int kStages = 3;
@@ -290,17 +117,6 @@ __device__ inline void issue_gather(const Stage<ND, NQ, HAS_K>& st, int m, int L
   cp_async_commit();
 }
 
-// barrier of the 128 threads of one warpgroup (named barrier 1 + g)
-__device__ __forceinline__ void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
-__device__ __forceinline__ bool wg_any(int g, bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.or.pred p, %2, 128, q;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(r)
-      : "r"(uint32_t(v)), "r"(1 + g)
-      : "memory");
-  return r != 0;
-}
 
 // One CTA = G warpgroups of 128 threads; each warpgroup runs the tile loop on
 // its own tiles with its own operand buffer, stages, mbarrier and TMEM
@@ -497,62 +313,8 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
       L_next2 = issue_meta<ND, NQ, HAS_K>(stage(b2), m, next2, tl_span, tl_list, tl_lidx, kcoef, nc);
     else
       cp_async_commit();
-    // 3. D_e per quadrature point, chunks of 16 points: G from TMEM, Q = (k_q) M_e g back into TMEM
-    //    (w_q is folded into the table of GEMM 2)
-    {
-#pragma unroll
-      for (int c = 0; c < S::NCHUNK; ++c) {
-        const int q0 = 16 * c;
-        const int nq = (NQ - q0) < 16 ? (NQ - q0) : 16;
-        const int nl = (3 * nq + 15) / 16;  // x16 loads in this chunk
-        uint32_t d[48];
-#pragma unroll
-        for (int l = 0; l < 3; ++l)
-          if (l < nl) tmem_ld16(lane_base + 48 * c + 16 * l, d + 16 * l);
-        tmem_wait_ld();
-#pragma unroll
-        for (int l = 0; l < 3; ++l)
-          if (l < nl) reg_fence16(d + 16 * l);
-        // Q overwrites G in the same registers: d[3i..3i+2] <- (k_q) M_e g_i
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          if (i < nq) {
-            const float gx = __uint_as_float(d[3 * i]), gy = __uint_as_float(d[3 * i + 1]),
-                        gz = __uint_as_float(d[3 * i + 2]);
-            float tx = fmaf(m0, gx, fmaf(m1, gy, m2 * gz));
-            float ty = fmaf(m1, gx, fmaf(m3, gy, m4 * gz));
-            float tz = fmaf(m2, gx, fmaf(m4, gy, m5 * gz));
-            if constexpr (HAS_K) {
-              const float kq = cur.kt[m * KS + q0 + i];
-              tx *= kq;
-              ty *= kq;
-              tz *= kq;
-            }
-            d[3 * i] = __float_as_uint(tx);
-            d[3 * i + 1] = __float_as_uint(ty);
-            d[3 * i + 2] = __float_as_uint(tz);
-          } else if (3 * i < 16 * nl) {
-            d[3 * i] = 0u;
-            if (3 * i + 1 < 16 * nl) d[3 * i + 1] = 0u;
-            if (3 * i + 2 < 16 * nl) d[3 * i + 2] = 0u;
-          }
-        }
-        if constexpr (BF16) {
-          uint32_t w[24];
-#pragma unroll
-          for (int i = 0; i < 24; ++i)
-            w[i] = pack_bf16(__uint_as_float(d[2 * i]), __uint_as_float(d[2 * i + 1]));
-#pragma unroll
-          for (int l = 0; l < 3; ++l)
-            if (l < nl) tmem_st8(lane_base + 24 * c + 8 * l, w + 8 * l);
-        } else {
-          // FP32 bits as the TF32 operand (the tensor core reads the top 19 bits)
-#pragma unroll
-          for (int l = 0; l < 3; ++l)
-            if (l < nl) tmem_st16(lane_base + 48 * c + 16 * l, d + 16 * l);
-        }
-      }
-    }
+    // 3. D_e per quadrature point: G in TMEM becomes Q = (k_q) M_e g_q (w_q is folded into the table of GEMM 2)
+    metric_to_q<ND, NQ, BF16, HAS_K>(lane_base, m0, m1, m2, m3, m4, m5, HAS_K ? cur.kt + m * KS : nullptr);
     tmem_wait_st();
     tc_fence_before();
     wg_sync(g);
@@ -589,24 +351,6 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(tmem_cols));
   if (failed && m == 0) atomicOr(status, 1);
-}
-
-// host: byte image of an operand stored K-major without swizzle
-template <bool BF16>
-void put_elem(std::vector<uint8_t>& img, size_t off, double v) {
-  float f = float(v);
-  uint32_t bits;
-  std::memcpy(&bits, &f, 4);
-  if (BF16) {
-    // round to nearest even
-    const uint32_t lsb = (bits >> 16) & 1u;
-    const uint16_t h = uint16_t((bits + 0x7FFFu + lsb) >> 16);
-    std::memcpy(&img[off], &h, 2);
-  } else {
-    // TF32, round to nearest with ties away from zero (as cvt.rna.tf32.f32)
-    bits = (bits + 0x1000u) & 0xFFFFE000u;
-    std::memcpy(&img[off], &bits, 4);
-  }
 }
 
 template <int ND, int NQ, bool BF16>

@@ -152,8 +152,9 @@ int upload(Ctx& c) {
     if (int s = put(c, &c.d_fb_geo32, cast<float>(c.fb_geo))) return s;
   }
   if (int s = put(c, &c.d_status, std::vector<int32_t>(4, 0))) return s;
-  if (c.kind == FEM_CG)
-    if (int s = tc_prepare(c)) return s;
+  if (int s = tc_prepare(c)) return s;  // E tables of the cell GEMMs (CG and DG)
+  if (c.kind == FEM_DG)
+    if (int s = dg_tc_prepare(c)) return s;
   TETMF_CK(cudaDeviceSynchronize());
   return FEM_OK;
 }

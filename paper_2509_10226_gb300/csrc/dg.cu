@@ -233,6 +233,19 @@ int launch_dg(Ctx& c, const T* u, T* y, const T* metric, const T* tab, const T* 
   return FEM_OK;
 }
 
+template <int ND, int NQF>
+int launch_boundary32(Ctx& c, const float* u, float* y, cudaStream_t st) {
+  if (c.nfb == 0) return FEM_OK;
+  const TableLayout L = tables_layout(c.tab);
+  const size_t sm_face = (size_t(4) * NQF * ND * 4 + NQF) * sizeof(float) + 6 * NQF * sizeof(int);
+  if (int e = allow_smem(k_dg_face_boundary<ND, NQF, float>, sm_face)) return e;
+  k_dg_face_boundary<ND, NQF, float><<<unsigned((c.nfb + kT - 1) / kT), kT, sm_face, st>>>(
+      c.d_fb_cell, c.d_fb_code, c.d_fb_geo32, c.d_tab32 + L.Vf, c.d_tab32 + L.Ef, c.d_tab32 + L.wf, c.d_fperm, u, y,
+      c.nfb);
+  TETMF_LAUNCH_CK();
+  return FEM_OK;
+}
+
 #define TETMF_DISPATCH_DG(p, CALL)                                                \
   switch (p) {                                                                   \
     case 1: { constexpr int ND = 4, NQ = 5, NQF = 4; return CALL; }               \
@@ -252,6 +265,11 @@ int dg_apply(Ctx& c, int prec, const void* u, void* y, void* stream) {
   }
   TETMF_DISPATCH_DG(c.p, (launch_dg<ND, NQ, NQF, float>(c, static_cast<const float*>(u), static_cast<float*>(y),
                                                         c.d_metric32, c.d_tab32, c.d_fi_geo32, c.d_fb_geo32, st)))
+}
+
+int dg_boundary_fp32(Ctx& c, const float* u, float* y, void* stream) {
+  cudaStream_t st = as_stream(stream);
+  TETMF_DISPATCH_DG(c.p, (launch_boundary32<ND, NQF>(c, u, y, st)))
 }
 
 }  // namespace tetmf

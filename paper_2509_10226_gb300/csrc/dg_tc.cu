@@ -1,0 +1,644 @@
+// Discontinuous Galerkin (SIPG, Eq. 2 / Eq. 5) apply with the interpolation
+// products on the tcgen05 tensor cores (TF32 or BF16 operands, FP32 accumulate).
+//
+// Cell loop (k_dg_cell_tc): the CG contraction of Eq. 3 on contiguous per-cell
+// DoFs, 128 cells per tile, difference form, Q in TMEM; y is written once per
+// cell (no atomics).
+//
+// Face loop (k_dg_face_tc): interior faces are grouped at set-up into tiles of
+// 128 faces that share the local face index of each side and the orientation
+// (96 combinations), so every face of a tile uses the same reference tables
+// ("faces with identical orientations share interpolation matrices", Sec. 3.1);
+// groups are padded with faces of zero weight.  Per tile:
+//   1. rows of U- and U+ (both sides' DoFs, shifted by the minus side's first
+//      DoF so that rounded tables keep jumps of smooth fields small: jumps and
+//      gradients are unchanged by a common shift);
+//   2. two GEMMs evaluate value and reference gradient at the face points:
+//      D = U . T^T with T = [phi; d phi / d xhat] (4 nqf x nd); the plus side's
+//      table has its points permuted into the minus side's order;
+//   3. per face and point the SIPG flux in FP32: jump, average normal
+//      derivative (a . grad_hat with a = J^-1 n), penalty; the coefficients of
+//      the test functions (value, and a * coefficient of the normal
+//      derivative) overwrite D in TMEM;
+//   4. two GEMMs integrate back, Y = Q . (w T) (weights folded in the table);
+//   5. both rows are added to y with vector atomics.
+// Boundary faces (2 % of the faces at 48^3) keep the FP32 SIMT kernel.
+#include <algorithm>
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
+#include "common.cuh"
+#include "tc_ptx.cuh"
+
+namespace tetmf {
+namespace {
+
+constexpr int kT = kTile;
+
+template <int ND, int NQF, bool BF16>
+struct FaceShape {
+  static constexpr int ES = BF16 ? 2 : 4;
+  static constexpr int KC = 16 / ES;
+  static constexpr int KSTEP = 2 * KC;
+  static constexpr int NE = round_up(4 * NQF, 16);      // evaluation GEMM N: (value, 3 gradients) per point
+  static constexpr int KE = round_up(ND, KSTEP);        // evaluation GEMM K
+  static constexpr int KI = round_up(4 * NQF, KSTEP);   // integration GEMM K
+  static constexpr int NI = round_up(ND, 16);           // integration GEMM N
+  static constexpr int QW = BF16 ? NE / 2 : NE;         // TMEM columns of the coefficients of one side
+  static constexpr int TCOLS = round_up(2 * NE + 2 * NI, 16);
+  static constexpr int GMAX = 512 / TCOLS < 4 ? 512 / TCOLS : 4;
+  static constexpr int LBO_A = (kT / 8) * 128;
+  static constexpr int LBO_E = (NE / 8) * 128;
+  static constexpr int LBO_I = (NI / 8) * 128;
+  static constexpr int A_BYTES = kT * KE * ES;
+  static constexpr int E_BYTES = NE * KE * ES;
+  static constexpr int I_BYTES = NI * KI * ES;
+  static constexpr uint32_t fmt = BF16 ? 1u : 2u;
+  __host__ __device__ static constexpr uint32_t idesc(int n) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(kT >> 4) << 24);
+  }
+  static_assert(KI <= NE, "coefficients must fit in the evaluation columns");
+};
+
+// Operand images: 4 minus evaluation tables (local face f), 24 plus evaluation tables
+// (local face f, orientation o: id 4 + 6 f + o), then the same 28 integration tables.
+
+template <int ND, int NQF, bool BF16>
+std::vector<uint8_t> face_images(const RefTables& t) {
+  using S = FaceShape<ND, NQF, BF16>;
+  std::vector<uint8_t> img(size_t(28) * S::E_BYTES + size_t(28) * S::I_BYTES, 0);
+  auto off = [](int r, int k, int lbo) {
+    return size_t((k / S::KC) * lbo + (r / 8) * 128 + (r % 8) * 16 + (k % S::KC) * S::ES);
+  };
+  // table entry: c = 0 value, c = 1..3 reference gradient, at point qq of local face f
+  auto entry = [&](int f, int qq, int c, int j) {
+    return c == 0 ? t.Vf[(size_t(f) * NQF + qq) * ND + j] : t.Ef[((size_t(f) * NQF + qq) * 3 + (c - 1)) * ND + j];
+  };
+  for (int id = 0; id < 28; ++id) {
+    const int f = id < 4 ? id : (id - 4) / 6;
+    const int o = id < 4 ? -1 : (id - 4) % 6;
+    uint8_t* E = img.data() + size_t(id) * S::E_BYTES;
+    uint8_t* I = img.data() + size_t(28) * S::E_BYTES + size_t(id) * S::I_BYTES;
+    std::vector<uint8_t> e(S::E_BYTES, 0), in(S::I_BYTES, 0);
+    for (int q = 0; q < NQF; ++q) {
+      const int qq = o < 0 ? q : t.fperm[o * NQF + q];  // plus side in the minus side's point order
+      for (int c = 0; c < 4; ++c)
+        for (int j = 0; j < ND; ++j) {
+          const double v = entry(f, qq, c, j);
+          put_elem<BF16>(e, off(4 * q + c, j, S::LBO_E), v);
+          put_elem<BF16>(in, off(j, 4 * q + c, S::LBO_I), v * t.wqf[q]);
+        }
+    }
+    std::memcpy(E, e.data(), e.size());
+    std::memcpy(I, in.data(), in.size());
+  }
+  return img;
+}
+
+template <int ND, int NQF>
+int prepare_images(Ctx& c) {
+  for (int b = 0; b < 2; ++b) {
+    const std::vector<uint8_t> img = b ? face_images<ND, NQF, true>(c.tab) : face_images<ND, NQF, false>(c.tab);
+    void* p = nullptr;
+    TETMF_CK(cudaMalloc(&p, img.size()));
+    c.allocations.push_back(p);
+    TETMF_CK(cudaMemcpy(p, img.data(), img.size(), cudaMemcpyHostToDevice));
+    (b ? c.d_dg_img_bf16 : c.d_dg_img_tf32) = p;
+  }
+  return FEM_OK;
+}
+
+// ---- cell loop ------------------------------------------------------------
+// Eq. 3 on contiguous per-cell DoFs (one offset per cell): 128 cells per tile, the tile's
+// 128 x ND block of u arrives in one coalesced copy (cp.async, 16-byte pieces) and y leaves the
+// same way, written once (the face kernels then add to it).  The GEMMs and the metric step are
+// the CG ones (difference form, E tables of the CG tensor-core path).
+template <int ND, int NQ, bool BF16>
+constexpr int cell_tcols() {
+  return round_up(TcShape<ND, NQ, BF16>::D2_COL + TcShape<ND, NQ, BF16>::N2, 16);
+}
+template <int ND, int NQ, bool BF16>
+constexpr int cell_gmax() {
+  return 512 / cell_tcols<ND, NQ, BF16>() < 4 ? 512 / cell_tcols<ND, NQ, BF16>() : 4;
+}
+template <int ND, int NQ, bool BF16>
+constexpr size_t cell_smem(int G) {
+  using S = TcShape<ND, NQ, BF16>;
+  return size_t(S::B1_BYTES) + S::B2_BYTES + size_t(G) * (32 + S::A1_BYTES + 2 * size_t(kT) * ND * 4);
+}
+
+// copy a tile's block of n floats (16-byte aligned source) into shared memory
+__device__ inline void issue_block(float* dst, const float* __restrict__ src, int n, int m) {
+  const int n4 = n / 4;
+  for (int i = m; i < n4; i += kT) cp_async16(dst + 4 * i, src + 4 * i);
+  for (int i = 4 * n4 + m; i < n; i += kT) cp_async4(dst + i, src + i);
+  cp_async_commit();
+}
+
+template <int ND, int NQ, bool BF16>
+__global__ void __launch_bounds__(kT * cell_gmax<ND, NQ, BF16>(), 1)
+    k_dg_cell_tc(const float* __restrict__ metric, const uint8_t* __restrict__ bimg, const float* __restrict__ u,
+                 float* __restrict__ y, int64_t nc, int64_t ntiles, uint32_t tmem_cols, int32_t* __restrict__ status) {
+  using S = TcShape<ND, NQ, BF16>;
+  constexpr int TCOLS = cell_tcols<ND, NQ, BF16>();
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int G = blockDim.x / kT;
+  const int g = threadIdx.x / kT;
+  const int m = threadIdx.x % kT;
+  const int warp = threadIdx.x >> 5;
+  uint8_t* misc = smem;  // [G][32]: mbarrier, TMEM slot (warpgroup 0)
+  uint8_t* sB1 = smem + 32 * G;
+  uint8_t* sB2 = sB1 + S::B1_BYTES;
+  uint8_t* own = sB2 + S::B2_BYTES + size_t(g) * (S::A1_BYTES + 2 * size_t(kT) * ND * 4);
+  uint8_t* sA1 = own;
+  float* const stg0 = reinterpret_cast<float*>(own + S::A1_BYTES);  // two stages of 128 x ND values
+  auto stg = [&](int i) { return stg0 + i * (kT * ND); };
+  uint64_t* bar = reinterpret_cast<uint64_t*>(misc + 32 * g);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 8);
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(bimg);
+    uint4* dst = reinterpret_cast<uint4*>(sB1);
+    for (int i = threadIdx.x; i < (S::B1_BYTES + S::B2_BYTES) / 16; i += blockDim.x) dst[i] = src[i];
+  }
+  const uint32_t bar_a = smem_u32(bar);
+  if (m == 0) mbar_init(bar_a);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  const int64_t stride = int64_t(gridDim.x) * G;
+  int64_t tile = int64_t(blockIdx.x) * G + g;
+  auto ncell_of = [&](int64_t t) { return int(nc - t * kT < kT ? nc - t * kT : kT); };
+  if (tile < ntiles) issue_block(stg(0), u + tile * kT * ND, ncell_of(tile) * ND, m);
+  else cp_async_commit();
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot + uint32_t(g * TCOLS);
+  const uint32_t lane_base = tmem + (uint32_t((warp & 3) * 32) << 16);
+  const uint32_t aA1 = smem_u32(sA1), aB1 = smem_u32(sB1), aB2 = smem_u32(sB2);
+  uint32_t phase = 0;
+  bool failed = false;
+  for (int b = 0; tile < ntiles; tile += stride, b ^= 1) {
+    const int64_t next = tile + stride;
+    if (next < ntiles) issue_block(stg(b ^ 1), u + next * kT * ND, ncell_of(next) * ND, m);
+    else cp_async_commit();
+    const int ncell = ncell_of(tile);
+    float* cur = stg(b);
+    cp_async_wait_group<1>();
+    wg_sync(g);
+    // 1. row m of U' (difference form); rows past the last cell are zero
+    {
+      float v1[S::K1];
+      const float ue0 = m < ncell ? cur[m * ND] : 0.0f;
+#pragma unroll
+      for (int j = 1; j < ND; ++j) v1[j - 1] = m < ncell ? cur[m * ND + j] - ue0 : 0.0f;
+#pragma unroll
+      for (int j = S::ND1; j < S::K1; ++j) v1[j] = 0.0f;
+      write_row<S::K1, BF16>(sA1, m, v1);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    wg_sync(g);
+    // 2. GEMM 1
+    if (m == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int s = 0; s < S::K1 / S::KSTEP; ++s)
+        mma<BF16>(tmem, smem_desc(aA1 + s * 2 * S::LBO_A, S::LBO_A, 128),
+                  smem_desc(aB1 + s * 2 * S::LBO_B1, S::LBO_B1, 128), S::idesc(S::N1), s > 0);
+      mma_commit(bar_a);
+    }
+    const float* mp = metric + tile * 6 * kT + m;
+    const float m0 = __ldg(mp), m1 = __ldg(mp + kT), m2 = __ldg(mp + 2 * kT), m3 = __ldg(mp + 3 * kT),
+                m4 = __ldg(mp + 4 * kT), m5 = __ldg(mp + 5 * kT);
+    if (m == 0) failed |= !mbar_wait(bar_a, phase);
+    phase ^= 1;
+    failed = wg_any(g, failed);
+    if (failed) break;
+    tc_fence_after();
+    // 3. D_e per quadrature point
+    metric_to_q<ND, NQ, BF16, false>(lane_base, m0, m1, m2, m3, m4, m5, nullptr);
+    tmem_wait_st();
+    tc_fence_before();
+    wg_sync(g);
+    // 4. GEMM 2 (A = Q in TMEM)
+    if (m == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int s = 0; s < S::K2 / S::KSTEP; ++s)
+        mma_ta<BF16>(tmem + S::D2_COL, tmem + 8 * s, smem_desc(aB2 + s * 2 * S::LBO_B2, S::LBO_B2, 128),
+                     S::idesc(S::N2), s > 0);
+      mma_commit(bar_a);
+      failed |= !mbar_wait(bar_a, phase);
+    }
+    phase ^= 1;
+    failed = wg_any(g, failed);
+    if (failed) break;
+    tc_fence_after();
+    // 5. row m of Y' from TMEM, y_0 = -sum, staged and written out coalesced
+    {
+      uint32_t r[S::N2];
+#pragma unroll
+      for (int c = 0; c < S::N2 / 16; ++c) tmem_ld16(lane_base + S::D2_COL + 16 * c, r + 16 * c);
+      tmem_wait_ld();
+#pragma unroll
+      for (int c = 0; c < S::N2 / 16; ++c) reg_fence16(r + 16 * c);
+      if (m < ncell) {
+        float y0 = 0.0f;
+#pragma unroll
+        for (int j = 1; j < ND; ++j) {
+          const float v = __uint_as_float(r[j - 1]);
+          cur[m * ND + j] = v;
+          y0 -= v;
+        }
+        cur[m * ND] = y0;
+      }
+    }
+    tc_fence_before();
+    wg_sync(g);
+    {
+      float* dst = y + tile * kT * ND;
+      const int n = ncell * ND, n4 = n / 4;
+      for (int i = m; i < n4; i += kT) reinterpret_cast<float4*>(dst)[i] = reinterpret_cast<const float4*>(cur)[i];
+      for (int i = 4 * n4 + m; i < n; i += kT) dst[i] = cur[i];
+    }
+    wg_sync(g);  // the stage is refilled by the prefetch of the next iteration
+  }
+  cp_async_wait_all();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(tmem_cols));
+  if (failed && m == 0) atomicOr(status, 1);
+}
+
+// ---- interior faces ---------------------------------------------------------
+template <int ND, int NQF, bool BF16>
+constexpr size_t face_wg_bytes() {
+  using S = FaceShape<ND, NQF, BF16>;
+  return 2 * size_t(S::E_BYTES) + 2 * size_t(S::I_BYTES) + 2 * size_t(S::A_BYTES);
+}
+
+// ND floats of one cell (contiguous; 16-byte aligned base, so cells of even ND are 8-byte
+// aligned and cells of ND % 4 == 0 are 16-byte aligned)
+template <int ND>
+__device__ __forceinline__ void load_cell(const float* __restrict__ p, float* v) {
+  if constexpr (ND % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < ND / 4; ++j) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(p) + j);
+      v[4 * j] = t.x, v[4 * j + 1] = t.y, v[4 * j + 2] = t.z, v[4 * j + 3] = t.w;
+    }
+  } else if constexpr (ND % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < ND / 2; ++j) {
+      const float2 t = __ldg(reinterpret_cast<const float2*>(p) + j);
+      v[2 * j] = t.x, v[2 * j + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < ND; ++j) v[j] = __ldg(p + j);
+  }
+}
+
+// y[0..ND) += v with vector reductions (no return value)
+template <int ND>
+__device__ __forceinline__ void red_cell(float* p, const uint32_t* v) {
+  if constexpr (ND % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < ND / 4; ++j)
+      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p + 4 * j), "f"(__uint_as_float(v[4 * j])),
+                   "f"(__uint_as_float(v[4 * j + 1])), "f"(__uint_as_float(v[4 * j + 2])),
+                   "f"(__uint_as_float(v[4 * j + 3]))
+                   : "memory");
+  } else if constexpr (ND % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < ND / 2; ++j)
+      asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p + 2 * j), "f"(__uint_as_float(v[2 * j])),
+                   "f"(__uint_as_float(v[2 * j + 1]))
+                   : "memory");
+  } else {
+#pragma unroll
+    for (int j = 0; j < ND; ++j) atomicAdd(p + j, __uint_as_float(v[j]));
+  }
+}
+
+// One CTA = G warpgroups; warpgroup w of the grid takes a contiguous run of tiles (tiles are
+// sorted by code, so a warpgroup reloads its four tables only when the code changes).
+// TMEM per warpgroup: D- [0, NE), D+ [NE, 2 NE) (coefficients overwrite them in place),
+// Y- [2 NE, 2 NE + NI), Y+ [2 NE + NI, 2 NE + 2 NI).
+template <int ND, int NQF, bool BF16>
+__global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
+    k_dg_face_tc(const int32_t* __restrict__ tcode, const int32_t* __restrict__ tcell, const float* __restrict__ tgeo,
+                 const uint8_t* __restrict__ img, const float* __restrict__ u, float* __restrict__ y, int64_t ntiles,
+                 uint32_t tmem_cols, int32_t* __restrict__ status) {
+  using S = FaceShape<ND, NQF, BF16>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int G = blockDim.x / kT;
+  const int g = threadIdx.x / kT;
+  const int m = threadIdx.x % kT;
+  const int warp = threadIdx.x >> 5;
+  uint8_t* misc = smem;
+  uint8_t* sEm = smem + 128 + size_t(g) * face_wg_bytes<ND, NQF, BF16>();
+  uint8_t* sEp = sEm + S::E_BYTES;
+  uint8_t* sIm = sEp + S::E_BYTES;
+  uint8_t* sIp = sIm + S::I_BYTES;
+  uint8_t* sAm = sIp + S::I_BYTES;
+  uint8_t* sAp = sAm + S::A_BYTES;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(misc + 16 * g);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 64);
+  const uint32_t bar_a = smem_u32(bar);
+  if (m == 0) mbar_init(bar_a);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot + uint32_t(g * S::TCOLS);
+  const uint32_t lane_base = tmem + (uint32_t((warp & 3) * 32) << 16);
+  const uint32_t aEm = smem_u32(sEm), aEp = smem_u32(sEp), aIm = smem_u32(sIm), aIp = smem_u32(sIp);
+  const uint32_t aAm = smem_u32(sAm), aAp = smem_u32(sAp);
+  const int64_t nw = int64_t(gridDim.x) * G;
+  const int64_t per = (ntiles + nw - 1) / nw;
+  const int64_t t0 = (int64_t(blockIdx.x) * G + g) * per;
+  const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
+  uint32_t phase = 0;
+  bool failed = false;
+  int code_loaded = -1;
+  for (int64_t t = t0; t < t1; ++t) {
+    const int code = __ldg(tcode + t);
+    // face data of the tile: cells of both sides, a- a+ 2|F| tau
+    const int64_t cm = __ldg(tcell + (t * 2) * kT + m), cp = __ldg(tcell + (t * 2 + 1) * kT + m);
+    float geo[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) geo[r] = __ldg(tgeo + (t * 8 + r) * kT + m);
+    float um[ND], up[ND];
+    load_cell<ND>(u + cm * ND, um);
+    load_cell<ND>(u + cp * ND, up);
+    if (code != code_loaded) {
+      // the four tables of this code (the previous tile's MMAs have completed)
+      const int fm = code / 24, fp = (code / 6) % 4, o = code % 6;
+      const uint4* ev = reinterpret_cast<const uint4*>(img);
+      const uint4* in = reinterpret_cast<const uint4*>(img + size_t(28) * S::E_BYTES);
+      constexpr int E16 = S::E_BYTES / 16, I16 = S::I_BYTES / 16;
+      for (int i = m; i < E16; i += kT) {
+        reinterpret_cast<uint4*>(sEm)[i] = __ldg(ev + size_t(fm) * E16 + i);
+        reinterpret_cast<uint4*>(sEp)[i] = __ldg(ev + size_t(4 + 6 * fp + o) * E16 + i);
+      }
+      for (int i = m; i < I16; i += kT) {
+        reinterpret_cast<uint4*>(sIm)[i] = __ldg(in + size_t(fm) * I16 + i);
+        reinterpret_cast<uint4*>(sIp)[i] = __ldg(in + size_t(4 + 6 * fp + o) * I16 + i);
+      }
+      code_loaded = code;
+    }
+    // 1. rows of U- and U+, both shifted by the minus side's first value
+    {
+      const float sh = um[0];
+      float v[S::KE];
+#pragma unroll
+      for (int j = 0; j < S::KE; ++j) v[j] = j < ND ? um[j] - sh : 0.0f;
+      write_row<S::KE, BF16>(sAm, m, v);
+#pragma unroll
+      for (int j = 0; j < S::KE; ++j) v[j] = j < ND ? up[j] - sh : 0.0f;
+      write_row<S::KE, BF16>(sAp, m, v);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    wg_sync(g);
+    // 2. evaluation GEMMs: value and reference gradient of both sides at the minus side's points
+    if (m == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int s = 0; s < S::KE / S::KSTEP; ++s) {
+        mma<BF16>(tmem, smem_desc(aAm + s * 2 * S::LBO_A, S::LBO_A, 128),
+                  smem_desc(aEm + s * 2 * S::LBO_E, S::LBO_E, 128), S::idesc(S::NE), s > 0);
+        mma<BF16>(tmem + S::NE, smem_desc(aAp + s * 2 * S::LBO_A, S::LBO_A, 128),
+                  smem_desc(aEp + s * 2 * S::LBO_E, S::LBO_E, 128), S::idesc(S::NE), s > 0);
+      }
+      mma_commit(bar_a);
+      failed |= !mbar_wait(bar_a, phase);
+    }
+    phase ^= 1;
+    failed = wg_any(g, failed);
+    if (failed) break;
+    tc_fence_after();
+    // 3. SIPG flux per point (Eq. 2): coefficients of the test functions' values and reference
+    //    gradients replace the evaluated values in TMEM, four points (16 columns) at a time
+    {
+      const float amx = geo[0], amy = geo[1], amz = geo[2], apx = geo[3], apy = geo[4], apz = geo[5];
+      const float sF = geo[6], tau = geo[7];
+#pragma unroll
+      for (int c = 0; c < S::NE / 16; ++c) {
+        uint32_t dm[16], dp[16];
+        tmem_ld16(lane_base + 16 * c, dm);
+        tmem_ld16(lane_base + S::NE + 16 * c, dp);
+        tmem_wait_ld();
+        reg_fence16(dm);
+        reg_fence16(dp);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (4 * c + i < NQF) {
+            const float vm = __uint_as_float(dm[4 * i]), vp = __uint_as_float(dp[4 * i]);
+            const float dnm = fmaf(amx, __uint_as_float(dm[4 * i + 1]),
+                                   fmaf(amy, __uint_as_float(dm[4 * i + 2]), amz * __uint_as_float(dm[4 * i + 3])));
+            const float dnp = fmaf(apx, __uint_as_float(dp[4 * i + 1]),
+                                   fmaf(apy, __uint_as_float(dp[4 * i + 2]), apz * __uint_as_float(dp[4 * i + 3])));
+            const float jump = vm - vp;
+            const float flux = sF * fmaf(0.5f, dnm + dnp, -tau * jump);  // 2|F| ({{dn u}} - tau [[u]])
+            const float cd = -0.5f * sF * jump;
+            dm[4 * i] = __float_as_uint(-flux);
+            dm[4 * i + 1] = __float_as_uint(amx * cd);
+            dm[4 * i + 2] = __float_as_uint(amy * cd);
+            dm[4 * i + 3] = __float_as_uint(amz * cd);
+            dp[4 * i] = __float_as_uint(flux);
+            dp[4 * i + 1] = __float_as_uint(apx * cd);
+            dp[4 * i + 2] = __float_as_uint(apy * cd);
+            dp[4 * i + 3] = __float_as_uint(apz * cd);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dm[4 * i + k] = dp[4 * i + k] = 0u;
+          }
+        }
+        if constexpr (BF16) {
+          uint32_t wm[8], wp[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            wm[i] = pack_bf16(__uint_as_float(dm[2 * i]), __uint_as_float(dm[2 * i + 1]));
+            wp[i] = pack_bf16(__uint_as_float(dp[2 * i]), __uint_as_float(dp[2 * i + 1]));
+          }
+          tmem_st8(lane_base + 8 * c, wm);
+          tmem_st8(lane_base + S::NE + 8 * c, wp);
+        } else {
+          tmem_st16(lane_base + 16 * c, dm);
+          tmem_st16(lane_base + S::NE + 16 * c, dp);
+        }
+      }
+    }
+    tmem_wait_st();
+    tc_fence_before();
+    wg_sync(g);
+    // 4. integration GEMMs (A = coefficients in TMEM, weights folded into the tables)
+    if (m == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int s = 0; s < S::KI / S::KSTEP; ++s) {
+        mma_ta<BF16>(tmem + 2 * S::NE, tmem + 8 * s, smem_desc(aIm + s * 2 * S::LBO_I, S::LBO_I, 128),
+                     S::idesc(S::NI), s > 0);
+        mma_ta<BF16>(tmem + 2 * S::NE + S::NI, tmem + S::NE + 8 * s,
+                     smem_desc(aIp + s * 2 * S::LBO_I, S::LBO_I, 128), S::idesc(S::NI), s > 0);
+      }
+      mma_commit(bar_a);
+      failed |= !mbar_wait(bar_a, phase);
+    }
+    phase ^= 1;
+    failed = wg_any(g, failed);
+    if (failed) break;
+    tc_fence_after();
+    // 5. both rows added to y (padding faces have 2|F| = 0 and add nothing)
+    {
+      uint32_t r[2 * S::NI];
+#pragma unroll
+      for (int c = 0; c < 2 * S::NI / 16; ++c) tmem_ld16(lane_base + 2 * S::NE + 16 * c, r + 16 * c);
+      tmem_wait_ld();
+#pragma unroll
+      for (int c = 0; c < 2 * S::NI / 16; ++c) reg_fence16(r + 16 * c);
+      if (geo[6] != 0.0f) {
+        red_cell<ND>(y + cm * ND, r);
+        red_cell<ND>(y + cp * ND, r + S::NI);
+      }
+    }
+    tc_fence_before();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(tmem_cols));
+  if (failed && m == 0) atomicOr(status, 1);
+}
+
+template <int ND, int NQ, int NQF, bool BF16>
+int launch_dg_tc(Ctx& c, const float* u, float* y, cudaStream_t st) {
+  int dev = 0, smem_max = 0;
+  TETMF_CK(cudaGetDevice(&dev));
+  TETMF_CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  {
+    // cell loop: as many warpgroups per CTA as TMEM and shared memory allow
+    int G = cell_gmax<ND, NQ, BF16>();
+    while (G > 1 && cell_smem<ND, NQ, BF16>(G) > size_t(smem_max)) --G;
+    const size_t sm = cell_smem<ND, NQ, BF16>(G);
+    if (sm > size_t(smem_max)) {
+      set_error("DG tensor-core cell kernel does not fit on an SM (%zu bytes of shared memory)", sm);
+      return FEM_EUNSUPPORTED;
+    }
+    auto kern = k_dg_cell_tc<ND, NQ, BF16>;
+    if (int e = allow_smem(kern, sm)) return e;
+    const uint32_t cols = uint32_t(pow2_cols(G * cell_tcols<ND, NQ, BF16>()));
+    int64_t grid = (c.ntiles + G - 1) / G;
+    if (grid > sm_count()) grid = sm_count();
+    if (grid > 0) {
+      kern<<<unsigned(grid), G * kT, sm, st>>>(c.d_metric32, static_cast<const uint8_t*>(BF16 ? c.d_tc_bf16 : c.d_tc_tf32),
+                                               u, y, c.nc, c.ntiles, cols, c.d_status);
+      TETMF_LAUNCH_CK();
+    }
+  }
+  if (c.dg_ntiles > 0) {
+    using S = FaceShape<ND, NQF, BF16>;
+    int G = S::GMAX;
+    while (G > 1 && 128 + G * face_wg_bytes<ND, NQF, BF16>() > size_t(smem_max)) --G;
+    const size_t sm = 128 + G * face_wg_bytes<ND, NQF, BF16>();
+    if (sm > size_t(smem_max)) {
+      set_error("DG tensor-core face kernel does not fit on an SM (%zu bytes of shared memory)", sm);
+      return FEM_EUNSUPPORTED;
+    }
+    auto kern = k_dg_face_tc<ND, NQF, BF16>;
+    if (int e = allow_smem(kern, sm)) return e;
+    const uint32_t cols = uint32_t(pow2_cols(G * S::TCOLS));
+    int64_t grid = (c.dg_ntiles + G - 1) / G;
+    if (grid > sm_count()) grid = sm_count();
+    kern<<<unsigned(grid), G * kT, sm, st>>>(c.d_dgt_code, c.d_dgt_cell, c.d_dgt_geo,
+                                             static_cast<const uint8_t*>(BF16 ? c.d_dg_img_bf16 : c.d_dg_img_tf32),
+                                             u, y, c.dg_ntiles, cols, c.d_status);
+    TETMF_LAUNCH_CK();
+  }
+  return dg_boundary_fp32(c, u, y, st);
+}
+
+}  // namespace
+
+int dg_tc_prepare(Ctx& c) {
+  // interior faces grouped by code, each group padded to whole tiles with zero-weight faces
+  std::vector<std::vector<int64_t>> groups(96);
+  for (int64_t i = 0; i < c.nfi; ++i) {
+    const int code = c.fi_code[i];
+    const int fm = code & 3, fp = (code >> 2) & 3, o = code >> 4;
+    groups[(fm * 4 + fp) * 6 + o].push_back(i);
+  }
+  int64_t nt = 0;
+  for (auto& g : groups) nt += (int64_t(g.size()) + kT - 1) / kT;
+  c.dg_ntiles = nt;
+  std::vector<int32_t> code(nt), cell(size_t(nt) * 2 * kT, 0);
+  std::vector<float> geo(size_t(nt) * 8 * kT, 0.0f);
+  int64_t t = 0;
+  for (int k = 0; k < 96; ++k) {
+    auto& g = groups[k];
+    std::sort(g.begin(), g.end(), [&](int64_t a, int64_t b) { return c.fi_cell[a] < c.fi_cell[b]; });
+    for (size_t s = 0; s < g.size(); s += kT, ++t) {
+      code[t] = k;
+      for (int m = 0; m < kT && s + m < g.size(); ++m) {
+        const int64_t i = g[s + m];
+        cell[(size_t(t) * 2 + 0) * kT + m] = c.fi_cell[i];
+        cell[(size_t(t) * 2 + 1) * kT + m] = c.fi_cell[c.nfi + i];
+        for (int r = 0; r < 8; ++r) geo[(size_t(t) * 8 + r) * kT + m] = float(c.fi_geo[size_t(r) * c.nfi + i]);
+      }
+    }
+  }
+  auto up = [&](auto** dst, const auto& v) -> int {
+    using T = typename std::remove_reference<decltype(v[0])>::type;
+    void* p = nullptr;
+    TETMF_CK(cudaMalloc(&p, std::max<size_t>(1, v.size()) * sizeof(T)));
+    c.allocations.push_back(p);
+    if (!v.empty()) TETMF_CK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *dst = static_cast<std::remove_const_t<T>*>(p);
+    return FEM_OK;
+  };
+  if (int s = up(&c.d_dgt_code, code)) return s;
+  if (int s = up(&c.d_dgt_cell, cell)) return s;
+  if (int s = up(&c.d_dgt_geo, geo)) return s;
+  switch (c.p) {
+    case 1: return prepare_images<4, 4>(c);
+    case 2: return prepare_images<10, 10>(c);
+    case 3: return prepare_images<20, 20>(c);
+    case 4: return prepare_images<35, 35>(c);
+  }
+  return FEM_OK;
+}
+
+}  // namespace tetmf
+
+namespace tetmf {
+
+int dg_apply_tc(Ctx& c, int prec, const void* u, void* y, void* stream) {
+  if ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(y)) & 15u) {
+    set_error("DG TF32/BF16 apply: u and y must be 16-byte aligned");
+    return FEM_EINVAL;
+  }
+  cudaStream_t st = as_stream(stream);
+  const float* uf = static_cast<const float*>(u);
+  float* yf = static_cast<float*>(y);
+  const bool bf = prec == FEM_BF16;
+  switch (c.p) {
+    case 1: return bf ? launch_dg_tc<4, 5, 4, true>(c, uf, yf, st) : launch_dg_tc<4, 5, 4, false>(c, uf, yf, st);
+    case 2: return bf ? launch_dg_tc<10, 15, 10, true>(c, uf, yf, st) : launch_dg_tc<10, 15, 10, false>(c, uf, yf, st);
+    case 3: return bf ? launch_dg_tc<20, 35, 20, true>(c, uf, yf, st) : launch_dg_tc<20, 35, 20, false>(c, uf, yf, st);
+    case 4: return bf ? launch_dg_tc<35, 70, 35, true>(c, uf, yf, st) : launch_dg_tc<35, 70, 35, false>(c, uf, yf, st);
+  }
+  set_error("degree %d not supported", c.p);
+  return FEM_EUNSUPPORTED;
+}
+
+}  // namespace tetmf

@@ -76,6 +76,13 @@ struct Ctx {
   // tensor-core operand images (shared-memory byte images of E^T and E)
   void* d_tc_tf32 = nullptr;
   void* d_tc_bf16 = nullptr;
+  // DG tensor-core face loop: interior faces in tiles of 128 faces sharing (f-, f+, orientation)
+  int64_t dg_ntiles = 0;
+  int32_t* d_dgt_code = nullptr;    // [dg_ntiles] (f- * 4 + f+) * 6 + o
+  int32_t* d_dgt_cell = nullptr;    // [dg_ntiles][2][128] minus, plus (padding faces: 0, 0)
+  float* d_dgt_geo = nullptr;       // [dg_ntiles][8][128] a-(3) a+(3) 2|F| tau (padding: 0)
+  void* d_dg_img_tf32 = nullptr;    // face evaluation and integration tables (56 operand images)
+  void* d_dg_img_bf16 = nullptr;
   // CSR comparator
   int64_t csr_nnz = 0;
   int64_t* d_csr_rowptr = nullptr;
@@ -113,6 +120,9 @@ int csr_build(Ctx& c, int64_t* nnz);
 int csr_apply(Ctx& c, int prec, const void* u, void* y, void* stream);
 int solve(Ctx& c, const fem_solve_opts* o, const double* b, double* x, fem_solve_stats* st, void* stream);
 int tc_prepare(Ctx& c);
+int dg_tc_prepare(Ctx& c);
+int dg_apply_tc(Ctx& c, int prec, const void* u, void* y, void* stream);
+int dg_boundary_fp32(Ctx& c, const float* u, float* y, void* stream);  // adds the boundary-face terms
 
 }  // namespace tetmf
 

@@ -604,8 +604,9 @@ int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k,
   Ctx& c = ctx->c;
   if (c.kind == FEM_DG) {
     if (k) return set_error("fem_apply: DG supports k = NULL only"), FEM_EUNSUPPORTED;
+    if (prec == FEM_TF32 || prec == FEM_BF16) return dg_apply_tc(c, prec, u, y, stream);
     if (prec != FEM_FP64 && prec != FEM_FP32)
-      return set_error("fem_apply: DG supports FEM_FP64 and FEM_FP32"), FEM_EUNSUPPORTED;
+      return set_error("fem_apply: unknown precision %d", prec), FEM_EUNSUPPORTED;
     return dg_apply(c, prec, u, y, stream);
   }
   switch (prec) {
@@ -627,8 +628,9 @@ int fem_apply_adjoint(fem_ctx* ctx, int32_t prec, const void* g, void* out, cons
   if (c.kind == FEM_DG) {
     // the SIPG form is symmetric: its adjoint is the same face/cell loop
     if (k) return set_error("fem_apply_adjoint: DG supports k = NULL only"), FEM_EUNSUPPORTED;
+    if (prec == FEM_TF32 || prec == FEM_BF16) return dg_apply_tc(c, prec, g, out, stream);
     if (prec != FEM_FP64 && prec != FEM_FP32)
-      return set_error("fem_apply_adjoint: DG supports FEM_FP64 and FEM_FP32"), FEM_EUNSUPPORTED;
+      return set_error("fem_apply_adjoint: unknown precision %d", prec), FEM_EUNSUPPORTED;
     return dg_apply(c, prec, g, out, stream);
   }
   if (prec != FEM_FP64 && prec != FEM_FP32)

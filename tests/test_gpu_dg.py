@@ -24,7 +24,7 @@ def lib_to_user(sp, v_lib):
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
 def test_dg_degrees(p, prec):
     from paper_2509_10226_gb300.fem import FemSpace
 
@@ -52,7 +52,7 @@ def test_dg_custom_penalty_and_adjoint():
     assert abs(v @ au - at @ u) < 1e-12 * abs(v @ au)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
 def test_config3_dg_p2_48cubed_sampled(prec):
     """DG SIPG P2 on the 48^3 Kuhn cube (663,552 cells, 1,313,280 interior + 27,648 boundary faces):
     256 sampled cells against the oracle evaluated on the sampled cells and their face neighbours."""
@@ -77,3 +77,32 @@ def test_config3_dg_p2_48cubed_sampled(prec):
     y_sub = dg.apply(xyz, cells[sub], u_sub, p).reshape(-1, nd)
     y_ref = y_sub[np.searchsorted(sub, sample)]
     assert_close(y_user.reshape(-1, nd)[sample], y_ref, prec, "config3 sampled")
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_dg_tensor_core_ragged_and_status(prec):
+    """Tensor-core DG on a mesh whose cell count is not a multiple of 128 and whose face groups
+    leave partial tiles; the device status word stays clean; a linear field (no jumps) keeps the
+    interior flux small, so the result tracks the FP64 apply to the stated tolerance."""
+    from paper_2509_10226_gb300.fem import FemSpace
+
+    p = 2
+    xyz, cells = synth.kuhn_cube(5, jitter=0.2, seed=3)  # 750 cells
+    sp = FemSpace(xyz, cells, kind="dg", degree=p, device=0)
+    assert sp.n_cells % 128 != 0
+    u = synth.uniform_vector(sp.n_dofs, 1)
+    y = to_host(sp.apply(to_dev(u, prec), prec=prec))
+    y64 = to_host(sp.apply(to_dev(u, "fp64")))
+    assert_close(y, y64, prec, "ragged")
+    assert sp.device_status() == 0
+    # smooth data: u(x) = a . x + b interpolated per cell (continuous across faces)
+    from oracle import basis
+
+    nodes = np.array(basis.nodes_beta(p), dtype=np.float64) / p  # barycentric weights of the nodes
+    perm = sp.cell_permutation()
+    X = np.einsum("nk,ckd->cnd", nodes, xyz[cells[perm]])  # library cell order
+    a = np.array([0.3, -1.1, 0.6])
+    ul = (X @ a + 0.25).ravel()
+    yl = to_host(sp.apply(to_dev(ul, prec), prec=prec))
+    yl64 = to_host(sp.apply(to_dev(ul, "fp64")))
+    assert_close(yl, yl64, prec, "linear field")
