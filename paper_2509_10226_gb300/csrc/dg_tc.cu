@@ -8,7 +8,7 @@
 // Face loop (k_dg_face_tc): interior faces are grouped at set-up into tiles of
 // 128 faces that share the local face index of each side and the orientation
 // (96 combinations), so every face of a tile uses the same reference tables
-// ("faces with identical orientations share interpolation matrices", Sec. 3.1);
+// (faces of equal orientation can share their interpolation matrices, Sec. 3.1);
 // groups are padded with faces of zero weight.  Per tile:
 //   1. rows of U- and U+ (both sides' DoFs, shifted by the minus side's first
 //      DoF so that rounded tables keep jumps of smooth fields small: jumps and
@@ -22,6 +22,8 @@
 //      derivative) overwrite D in TMEM;
 //   4. two GEMMs integrate back, Y = Q . (w T) (weights folded in the table);
 //   5. both rows are added to y with vector atomics.
+// The rows of U live in TMEM (the A operand of the evaluation GEMMs), and the
+// DoF values and face data of the next tiles are copied ahead (cp.async).
 // Boundary faces (2 % of the faces at 48^3) keep the FP32 SIMT kernel.
 #include <algorithm>
 #include <cstring>
@@ -48,10 +50,8 @@ struct FaceShape {
   static constexpr int QW = BF16 ? NE / 2 : NE;         // TMEM columns of the coefficients of one side
   static constexpr int TCOLS = round_up(2 * NE + 2 * NI, 16);
   static constexpr int GMAX = 512 / TCOLS < 4 ? 512 / TCOLS : 4;
-  static constexpr int LBO_A = (kT / 8) * 128;
   static constexpr int LBO_E = (NE / 8) * 128;
   static constexpr int LBO_I = (NI / 8) * 128;
-  static constexpr int A_BYTES = kT * KE * ES;
   static constexpr int E_BYTES = NE * KE * ES;
   static constexpr int I_BYTES = NI * KI * ES;
   static constexpr uint32_t fmt = BF16 ? 1u : 2u;
@@ -276,66 +276,134 @@ __global__ void __launch_bounds__(kT * cell_gmax<ND, NQ, BF16>(), 1)
 }
 
 // ---- interior faces ---------------------------------------------------------
+constexpr int kMetaWords = 11 * kTile;  // one slot of face data (see issue_face_meta)
+
 template <int ND, int NQF, bool BF16>
 constexpr size_t face_wg_bytes() {
   using S = FaceShape<ND, NQF, BF16>;
-  return 2 * size_t(S::E_BYTES) + 2 * size_t(S::I_BYTES) + 2 * size_t(S::A_BYTES);
+  // tables, DoF values of both sides (one slot), face data (two slots)
+  return 2 * size_t(S::E_BYTES) + 2 * size_t(S::I_BYTES) + 2 * size_t(kT) * ND * 4 + 2 * size_t(kMetaWords) * 4;
 }
 
-// ND floats of one cell (contiguous; 16-byte aligned base, so cells of even ND are 8-byte
-// aligned and cells of ND % 4 == 0 are 16-byte aligned)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// face data of tile t into a slot [11][128]: cells of both sides, a- a+ 2|F| tau (5 KB), and
+// the tile's code in word 10 * 128
+__device__ __forceinline__ void issue_face_meta(uint32_t* slot, const int32_t* __restrict__ tcode,
+                                                const int32_t* __restrict__ tcell, const float* __restrict__ tgeo,
+                                                int64_t t, int m) {
+  for (int i = m; i < 2 * kT / 4; i += kT) cp_async16(slot + 4 * i, tcell + t * 2 * kT + 4 * i);
+  for (int i = m; i < 8 * kT / 4; i += kT) cp_async16(slot + 2 * kT + 4 * i, tgeo + t * 8 * kT + 4 * i);
+  if (m == 0) cp_async4(slot + 10 * kT, tcode + t);
+}
+
+// one staged row of ND values (64-bit shared loads for even ND: rows 40 bytes apart then fill
+// the two wavefronts of a warp's request without bank conflicts)
 template <int ND>
-__device__ __forceinline__ void load_cell(const float* __restrict__ p, float* v) {
-  if constexpr (ND % 4 == 0) {
-#pragma unroll
-    for (int j = 0; j < ND / 4; ++j) {
-      const float4 t = __ldg(reinterpret_cast<const float4*>(p) + j);
-      v[4 * j] = t.x, v[4 * j + 1] = t.y, v[4 * j + 2] = t.z, v[4 * j + 3] = t.w;
-    }
-  } else if constexpr (ND % 2 == 0) {
+__device__ __forceinline__ void load_row(const float* r, float* v) {
+  if constexpr (ND % 2 == 0) {
 #pragma unroll
     for (int j = 0; j < ND / 2; ++j) {
-      const float2 t = __ldg(reinterpret_cast<const float2*>(p) + j);
+      const float2 t = reinterpret_cast<const float2*>(r)[j];
       v[2 * j] = t.x, v[2 * j + 1] = t.y;
     }
   } else {
 #pragma unroll
-    for (int j = 0; j < ND; ++j) v[j] = __ldg(p + j);
+    for (int j = 0; j < ND; ++j) v[j] = r[j];
   }
 }
 
-// y[0..ND) += v with vector reductions (no return value)
+// this thread's rows of the tile: the DoF values of its face's two cells
+template <int ND>
+__device__ __forceinline__ void issue_face_u(float* su, const float* __restrict__ u, int64_t cm, int64_t cp, int m) {
+  float* dm = su + m * ND;
+  float* dp = su + (kT + m) * ND;
+  const float* a = u + cm * ND;
+  const float* b = u + cp * ND;
+  if constexpr (ND % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < ND; j += 4) cp_async16(dm + j, a + j), cp_async16(dp + j, b + j);
+  } else if constexpr (ND % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < ND; j += 2) cp_async8(dm + j, a + j), cp_async8(dp + j, b + j);
+  } else {
+#pragma unroll
+    for (int j = 0; j < ND; ++j) cp_async4(dm + j, a + j), cp_async4(dp + j, b + j);
+  }
+}
+
+__device__ __forceinline__ void red_v4(float* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(__uint_as_float(a)), "f"(__uint_as_float(b)),
+               "f"(__uint_as_float(c)), "f"(__uint_as_float(d))
+               : "memory");
+}
+__device__ __forceinline__ void red_v2(float* p, uint32_t a, uint32_t b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(__uint_as_float(a)), "f"(__uint_as_float(b))
+               : "memory");
+}
+
+// y[0..ND) += v with vector reductions (no return value).  Rows of ND = 2 mod 4 values start on
+// an 8-byte boundary: 16-byte pieces where the row is 16-byte aligned, else one 8-byte piece
+// first; the operands are selected without divergence.
 template <int ND>
 __device__ __forceinline__ void red_cell(float* p, const uint32_t* v) {
   if constexpr (ND % 4 == 0) {
 #pragma unroll
-    for (int j = 0; j < ND / 4; ++j)
-      asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p + 4 * j), "f"(__uint_as_float(v[4 * j])),
-                   "f"(__uint_as_float(v[4 * j + 1])), "f"(__uint_as_float(v[4 * j + 2])),
-                   "f"(__uint_as_float(v[4 * j + 3]))
-                   : "memory");
+    for (int j = 0; j < ND / 4; ++j) red_v4(p + 4 * j, v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
   } else if constexpr (ND % 2 == 0) {
+    const bool a16 = (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+    const int o4 = a16 ? 0 : 2;
 #pragma unroll
-    for (int j = 0; j < ND / 2; ++j)
-      asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p + 2 * j), "f"(__uint_as_float(v[2 * j])),
-                   "f"(__uint_as_float(v[2 * j + 1]))
-                   : "memory");
+    for (int j = 0; j < ND / 4; ++j)
+      red_v4(p + o4 + 4 * j, a16 ? v[4 * j] : v[4 * j + 2], a16 ? v[4 * j + 1] : v[4 * j + 3],
+             a16 ? v[4 * j + 2] : v[4 * j + 4], a16 ? v[4 * j + 3] : v[4 * j + 5]);
+    red_v2(p + (a16 ? ND - 2 : 0), a16 ? v[ND - 2] : v[0], a16 ? v[ND - 1] : v[1]);
   } else {
 #pragma unroll
     for (int j = 0; j < ND; ++j) atomicAdd(p + j, __uint_as_float(v[j]));
   }
 }
 
+// one row of U (values minus the shift, zero past ND) as TMEM words: FP32 bits (TF32 operand)
+// or packed BF16 pairs
+template <int ND, int KE, bool BF16>
+__device__ __forceinline__ void pack_row(const float* v, float sh, uint32_t* w) {
+  if constexpr (BF16) {
+#pragma unroll
+    for (int j = 0; j < KE / 2; ++j)
+      w[j] = pack_bf16(2 * j < ND ? v[2 * j] - sh : 0.0f, 2 * j + 1 < ND ? v[2 * j + 1] - sh : 0.0f);
+  } else {
+#pragma unroll
+    for (int j = 0; j < KE; ++j) w[j] = __float_as_uint(j < ND ? v[j] - sh : 0.0f);
+  }
+}
+
+// W consecutive TMEM columns of this thread's lane (W a multiple of 8)
+template <int W>
+__device__ __forceinline__ void tmem_st_row(uint32_t taddr, const uint32_t* w) {
+#pragma unroll
+  for (int c = 0; c + 16 <= W; c += 16) tmem_st16(taddr + c, w + c);
+  if constexpr (W % 16 == 8) tmem_st8(taddr + (W - 8), w + (W - 8));
+}
+
 // One CTA = G warpgroups; warpgroup w of the grid takes a contiguous run of tiles (tiles are
-// sorted by code, so a warpgroup reloads its four tables only when the code changes).
+// sorted by code, so a warpgroup reloads its tables only when the code changes).
 // TMEM per warpgroup: D- [0, NE), D+ [NE, 2 NE) (coefficients overwrite them in place),
-// Y- [2 NE, 2 NE + NI), Y+ [2 NE + NI, 2 NE + 2 NI).
+// Y- [2 NE, 2 NE + NI), Y+ [2 NE + NI, 2 NE + 2 NI).  The rows U-, U+ (the A operands of the
+// evaluation GEMMs) are stored by each thread into its own lane of the Y columns, which the
+// integration GEMMs overwrite only after the evaluation GEMMs have completed.
+// The DoF values of tile t+1 and the face data of tile t+2 are copied (cp.async) while tile t
+// is computed.
 template <int ND, int NQF, bool BF16>
 __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
     k_dg_face_tc(const int32_t* __restrict__ tcode, const int32_t* __restrict__ tcell, const float* __restrict__ tgeo,
                  const uint8_t* __restrict__ img, const float* __restrict__ u, float* __restrict__ y, int64_t ntiles,
                  uint32_t tmem_cols, int32_t* __restrict__ status) {
   using S = FaceShape<ND, NQF, BF16>;
+  constexpr int AW = BF16 ? S::KE / 2 : S::KE;  // TMEM columns of one row of U
+  static_assert(AW <= S::NI && AW % 8 == 0, "rows of U must fit in the Y columns");
   extern __shared__ __align__(1024) uint8_t smem[];
   const int G = blockDim.x / kT;
   const int g = threadIdx.x / kT;
@@ -346,8 +414,8 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
   uint8_t* sEp = sEm + S::E_BYTES;
   uint8_t* sIm = sEp + S::E_BYTES;
   uint8_t* sIp = sIm + S::I_BYTES;
-  uint8_t* sAm = sIp + S::I_BYTES;
-  uint8_t* sAp = sAm + S::A_BYTES;
+  float* sU = reinterpret_cast<float*>(sIp + S::I_BYTES);           // [2 sides][128][ND] (own rows)
+  uint32_t* sMeta = reinterpret_cast<uint32_t*>(sU + 2 * kT * ND);  // [2][kMetaWords]
   uint64_t* bar = reinterpret_cast<uint64_t*>(misc + 16 * g);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 64);
   const uint32_t bar_a = smem_u32(bar);
@@ -362,8 +430,8 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
   tc_fence_after();
   const uint32_t tmem = *tslot + uint32_t(g * S::TCOLS);
   const uint32_t lane_base = tmem + (uint32_t((warp & 3) * 32) << 16);
+  constexpr uint32_t YM = 2 * S::NE, YP = 2 * S::NE + S::NI;  // Y- / U- and Y+ / U+ columns
   const uint32_t aEm = smem_u32(sEm), aEp = smem_u32(sEp), aIm = smem_u32(sIm), aIp = smem_u32(sIp);
-  const uint32_t aAm = smem_u32(sAm), aAp = smem_u32(sAp);
   const int64_t nw = int64_t(gridDim.x) * G;
   const int64_t per = (ntiles + nw - 1) / nw;
   const int64_t t0 = (int64_t(blockIdx.x) * G + g) * per;
@@ -371,18 +439,30 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
   uint32_t phase = 0;
   bool failed = false;
   int code_loaded = -1;
+  if (t0 < t1) {
+    // prologue: face data of t0, then the values of t0 and the face data of t0+1
+    issue_face_meta(sMeta, tcode, tcell, tgeo, t0, m);
+    cp_async_commit();
+    cp_async_wait_group<0>();
+    wg_sync(g);
+    issue_face_u<ND>(sU, u, int64_t(int32_t(sMeta[m])), int64_t(int32_t(sMeta[kT + m])), m);
+    if (t0 + 1 < t1) issue_face_meta(sMeta + kMetaWords, tcode, tcell, tgeo, t0 + 1, m);
+    cp_async_commit();
+  }
   for (int64_t t = t0; t < t1; ++t) {
-    const int code = __ldg(tcode + t);
+    const int sl = int(t - t0) & 1;
+    const uint32_t* meta = sMeta + sl * kMetaWords;
+    uint32_t* meta_next = sMeta + (sl ^ 1) * kMetaWords;
+    cp_async_wait_group<0>();  // this tile's values (own rows) and the next tile's face data
+    wg_sync(g);
     // face data of the tile: cells of both sides, a- a+ 2|F| tau
-    const int64_t cm = __ldg(tcell + (t * 2) * kT + m), cp = __ldg(tcell + (t * 2 + 1) * kT + m);
+    const int64_t cm = int32_t(meta[m]), cp = int32_t(meta[kT + m]);
     float geo[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) geo[r] = __ldg(tgeo + (t * 8 + r) * kT + m);
-    float um[ND], up[ND];
-    load_cell<ND>(u + cm * ND, um);
-    load_cell<ND>(u + cp * ND, up);
+    for (int r = 0; r < 8; ++r) geo[r] = __uint_as_float(meta[(2 + r) * kT + m]);
+    const int code = int32_t(meta[10 * kT]);
     if (code != code_loaded) {
-      // the four tables of this code (the previous tile's MMAs have completed)
+      // the four tables of this code (every MMA of the previous tile has completed)
       const int fm = code / 24, fp = (code / 6) % 4, o = code % 6;
       const uint4* ev = reinterpret_cast<const uint4*>(img);
       const uint4* in = reinterpret_cast<const uint4*>(img + size_t(28) * S::E_BYTES);
@@ -395,20 +475,22 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
         reinterpret_cast<uint4*>(sIm)[i] = __ldg(in + size_t(fm) * I16 + i);
         reinterpret_cast<uint4*>(sIp)[i] = __ldg(in + size_t(4 + 6 * fp + o) * I16 + i);
       }
+      fence_proxy_async();
       code_loaded = code;
     }
-    // 1. rows of U- and U+, both shifted by the minus side's first value
+    // 1. rows of U- and U+ (shifted by the minus side's first value) into this thread's TMEM lane
     {
+      float um[ND], up[ND];
+      load_row<ND>(sU + m * ND, um);
+      load_row<ND>(sU + (kT + m) * ND, up);
       const float sh = um[0];
-      float v[S::KE];
-#pragma unroll
-      for (int j = 0; j < S::KE; ++j) v[j] = j < ND ? um[j] - sh : 0.0f;
-      write_row<S::KE, BF16>(sAm, m, v);
-#pragma unroll
-      for (int j = 0; j < S::KE; ++j) v[j] = j < ND ? up[j] - sh : 0.0f;
-      write_row<S::KE, BF16>(sAp, m, v);
+      uint32_t w[AW];
+      pack_row<ND, S::KE, BF16>(um, sh, w);
+      tmem_st_row<AW>(lane_base + YM, w);
+      pack_row<ND, S::KE, BF16>(up, sh, w);
+      tmem_st_row<AW>(lane_base + YP, w);
     }
-    fence_proxy_async();
+    tmem_wait_st();
     tc_fence_before();
     wg_sync(g);
     // 2. evaluation GEMMs: value and reference gradient of both sides at the minus side's points
@@ -416,14 +498,19 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
       tc_fence_after();
 #pragma unroll
       for (int s = 0; s < S::KE / S::KSTEP; ++s) {
-        mma<BF16>(tmem, smem_desc(aAm + s * 2 * S::LBO_A, S::LBO_A, 128),
-                  smem_desc(aEm + s * 2 * S::LBO_E, S::LBO_E, 128), S::idesc(S::NE), s > 0);
-        mma<BF16>(tmem + S::NE, smem_desc(aAp + s * 2 * S::LBO_A, S::LBO_A, 128),
-                  smem_desc(aEp + s * 2 * S::LBO_E, S::LBO_E, 128), S::idesc(S::NE), s > 0);
+        mma_ta<BF16>(tmem, tmem + YM + 8 * s, smem_desc(aEm + s * 2 * S::LBO_E, S::LBO_E, 128), S::idesc(S::NE),
+                     s > 0);
+        mma_ta<BF16>(tmem + S::NE, tmem + YP + 8 * s, smem_desc(aEp + s * 2 * S::LBO_E, S::LBO_E, 128),
+                     S::idesc(S::NE), s > 0);
       }
       mma_commit(bar_a);
-      failed |= !mbar_wait(bar_a, phase);
     }
+    // prefetch: values of tile t+1 (this thread's rows of tile t are consumed) and face data of
+    // tile t+2 (into the slot read above, before the barrier)
+    if (t + 1 < t1) issue_face_u<ND>(sU, u, int64_t(int32_t(meta_next[m])), int64_t(int32_t(meta_next[kT + m])), m);
+    if (t + 2 < t1) issue_face_meta(const_cast<uint32_t*>(meta), tcode, tcell, tgeo, t + 2, m);
+    cp_async_commit();
+    if (m == 0) failed |= !mbar_wait(bar_a, phase);
     phase ^= 1;
     failed = wg_any(g, failed);
     if (failed) break;
@@ -483,15 +570,16 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
     tmem_wait_st();
     tc_fence_before();
     wg_sync(g);
-    // 4. integration GEMMs (A = coefficients in TMEM, weights folded into the tables)
+    // 4. integration GEMMs (A = coefficients in TMEM, weights folded into the tables); they
+    //    overwrite the rows of U, whose GEMMs have completed
     if (m == 0) {
       tc_fence_after();
 #pragma unroll
       for (int s = 0; s < S::KI / S::KSTEP; ++s) {
-        mma_ta<BF16>(tmem + 2 * S::NE, tmem + 8 * s, smem_desc(aIm + s * 2 * S::LBO_I, S::LBO_I, 128),
+        mma_ta<BF16>(tmem + YM, tmem + 8 * s, smem_desc(aIm + s * 2 * S::LBO_I, S::LBO_I, 128), S::idesc(S::NI),
+                     s > 0);
+        mma_ta<BF16>(tmem + YP, tmem + S::NE + 8 * s, smem_desc(aIp + s * 2 * S::LBO_I, S::LBO_I, 128),
                      S::idesc(S::NI), s > 0);
-        mma_ta<BF16>(tmem + 2 * S::NE + S::NI, tmem + S::NE + 8 * s,
-                     smem_desc(aIp + s * 2 * S::LBO_I, S::LBO_I, 128), S::idesc(S::NI), s > 0);
       }
       mma_commit(bar_a);
       failed |= !mbar_wait(bar_a, phase);
@@ -500,21 +588,20 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
     failed = wg_any(g, failed);
     if (failed) break;
     tc_fence_after();
-    // 5. both rows added to y (padding faces have 2|F| = 0 and add nothing)
-    {
-      uint32_t r[2 * S::NI];
+    // 5. both rows added to y, one side at a time (padding faces have 2|F| = 0 and add nothing)
 #pragma unroll
-      for (int c = 0; c < 2 * S::NI / 16; ++c) tmem_ld16(lane_base + 2 * S::NE + 16 * c, r + 16 * c);
+    for (int side = 0; side < 2; ++side) {
+      uint32_t r[S::NI];
+#pragma unroll
+      for (int c = 0; c < S::NI / 16; ++c) tmem_ld16(lane_base + (side ? YP : YM) + 16 * c, r + 16 * c);
       tmem_wait_ld();
 #pragma unroll
-      for (int c = 0; c < 2 * S::NI / 16; ++c) reg_fence16(r + 16 * c);
-      if (geo[6] != 0.0f) {
-        red_cell<ND>(y + cm * ND, r);
-        red_cell<ND>(y + cp * ND, r + S::NI);
-      }
+      for (int c = 0; c < S::NI / 16; ++c) reg_fence16(r + 16 * c);
+      if (geo[6] != 0.0f) red_cell<ND>(y + (side ? cp : cm) * ND, r);
     }
     tc_fence_before();
   }
+  cp_async_wait_all();
   tc_fence_before();
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(tmem_cols));
