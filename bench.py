@@ -53,23 +53,27 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "source": "fallback", "sm_max_mhz": 2070.0}
 
 
-def profiled_traffic(kernel_source, summary):
+def profiled_traffic(kernel_sources, summary):
     """DRAM bytes per launch recorded by an ncu capture in profiles/<summary>, if that capture was taken of
-    the current kernel source (same sha1), else None."""
+    the current kernel sources (sha1 of the files concatenated in the given order), else None."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", summary)
-    src = os.path.join(ROOT, "paper_2509_10226_gb300", "csrc", kernel_source)
-    if not (os.path.exists(path) and os.path.exists(src)):
+    srcs = [os.path.join(ROOT, "paper_2509_10226_gb300", "csrc", k) for k in kernel_sources]
+    if not (os.path.exists(path) and all(os.path.exists(p) for p in srcs)):
         return None
-    with open(src, "rb") as f:
-        digest = hashlib.sha1(f.read()).hexdigest()
+    h = hashlib.sha1()
+    for p in srcs:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    digest = h.hexdigest()
     rec = {}
     with open(path) as f:
         for line in f:
             if ":" in line and line.strip().startswith("- "):
                 k, v = line.strip()[2:].split(":", 1)
-                rec[k.strip()] = v.strip().strip("`")
+                v = v.strip()
+                rec[k.strip()] = v.split("`")[1] if v.startswith("`") else v.split()[0] if v else v
     if rec.get("source_sha1") != digest:
         return None
     try:
@@ -265,6 +269,7 @@ def main():
     ap.add_argument("--n", type=int, default=64, help="subcubes per direction of the CG workload")
     ap.add_argument("--no-variants", action="store_true", help="time the headline apply only")
     ap.add_argument("--no-dg", action="store_true")
+    ap.add_argument("--no-reorder", action="store_true", help="skip the shuffled-mesh reordering ablation")
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -327,7 +332,7 @@ def main():
     y_head = y32.double().clone()
     hb = cg_bytes(C, N, nd, head)
     achieved = hb / (t_head * 1e-3) / 1e9
-    traffic = profiled_traffic("cg_tc.cu", "k_cg_apply_tc.cg_p3_64.md") if n == 64 else None
+    traffic = profiled_traffic(["cg_tc.cu", "tc_ptx.cuh"], "k_cg_apply_tc.cg_p3_64.md") if n == 64 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "algorithmic_bytes": hb,
                 "kernel": "fem_apply tf32 (zero-fill + k_cg_apply_tc)",
@@ -394,6 +399,24 @@ def main():
                                                "rel_l2_vs_fp64": rel(y_), "build_s": build_s}
             except Exception as e:  # noqa: BLE001
                 variants["csr"] = {"unavailable": str(e).splitlines()[0]}
+        if not args.no_reorder:
+            # Sec. 2.5 ablation: the same cube with cells and vertices shuffled (generator order), applied
+            # in that order and after the Morton renumbering
+            try:
+                xs, cs, _ = synth.shuffle_mesh(xyz, cells, seed=synth.SEEDS["shuffle"])
+                for tag, ro in (("none", False), ("morton", True)):
+                    ssp = FemSpace(xs, cs, kind="cg", degree=p, reorder=ro, device=local)
+                    su = torch.as_tensor(synth.uniform_vector(ssp.n_dofs, synth.SEEDS["u"]), device="cuda",
+                                         dtype=torch.float32)
+                    sy = torch.empty_like(su)
+                    for prec in ("tf32", "fp32"):
+                        msv = time_steps(torch, lambda: ssp.apply(su, prec=prec, out=sy), vsteps, 2, flush, stream,
+                                         barrier)
+                        t = float(np.mean(msv))
+                        variants[f"shuffled_reorder_{tag}_{prec}"] = {"gdofs": ssp.n_dofs / (t * 1e-3) / 1e9, "ms": t}
+                    del ssp, su, sy
+            except Exception as e:  # noqa: BLE001
+                variants["shuffled_reorder"] = {"unavailable": str(e).splitlines()[0]}
         if not args.no_solve:
             try:
                 variants["solve_cg_p3_48"] = time_solves(torch, FemSpace, local)

@@ -137,6 +137,11 @@ int fem_dof_permutation(const fem_ctx* ctx, int64_t* lib_to_canonical);
  * library DoF i (vertex v_m of a cell repeated beta_m times).  Array N*p. */
 int fem_dof_keys(const fem_ctx* ctx, int32_t* keys);
 
+/* xyz[i][0..2] = physical position of the node of library DoF i (the point
+ * where its shape function is 1): sum_m beta_m x_m / p over the vertices x_m
+ * of a cell containing it.  Array N*3 of double, host memory. */
+int fem_dof_coordinates(const fem_ctx* ctx, double* xyz);
+
 /* CG only: mask[i] = 1 if library DoF i is Dirichlet-constrained.  Array N. */
 int fem_dirichlet_mask(const fem_ctx* ctx, uint8_t* mask);
 

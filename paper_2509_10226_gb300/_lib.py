@@ -61,6 +61,7 @@ _SIGNATURES = {
     "fem_cell_permutation": [_P, _P],
     "fem_dof_permutation": [_P, _P],
     "fem_dof_keys": [_P, _P],
+    "fem_dof_coordinates": [_P, _P],
     "fem_dirichlet_mask": [_P, _P],
     "fem_device_status": [_P, _P],
     "fem_apply": [_P, ctypes.c_int32, _P, _P, _P, _P],

@@ -35,6 +35,8 @@ struct Ctx {
   int64_t nv = 0, nc = 0, ndofs = 0, ntiles = 0;
   RefTables tab;
   std::vector<int32_t> cell_perm;   // lib -> user
+  std::vector<double> xyz;          // [nv][3] user vertex coordinates (copy)
+  std::vector<int32_t> ucells;      // [nc][4] user cells (copy)
   std::vector<int32_t> cell_dofs;   // [nc][nd] lib DoF ids (CG; unmasked)
   std::vector<int32_t> dof_keys;    // [ndofs][p] (CG)
   std::vector<int64_t> dof_canon;   // lib DoF -> canonical DoF

@@ -110,6 +110,8 @@ int build_plan(Ctx& c, const fem_mesh_desc* m) {
   const double* xyz = m->xyz;
   const int32_t* ucells = m->cells;
   const int64_t nc = c.nc;
+  c.xyz.assign(xyz, xyz + 3 * c.nv);
+  c.ucells.assign(ucells, ucells + 4 * nc);
 
   // validation (vertex range, degenerate cells)
   for (int64_t e = 0; e < nc; ++e)
@@ -581,6 +583,37 @@ int fem_dof_keys(const fem_ctx* ctx, int32_t* keys) {
   if (!keys) return set_error("null output"), FEM_EINVAL;
   if (ctx->c.kind != FEM_CG) return set_error("fem_dof_keys: CG spaces only"), FEM_EINVAL;
   std::memcpy(keys, ctx->c.dof_keys.data(), sizeof(int32_t) * ctx->c.dof_keys.size());
+  return FEM_OK;
+}
+
+int fem_dof_coordinates(const fem_ctx* ctx, double* xyz) {
+  if (int s = check_ctx(ctx)) return s;
+  if (!xyz) return set_error("null output"), FEM_EINVAL;
+  const Ctx& c = ctx->c;
+  if (c.kind == FEM_CG) {
+    // the node of a DoF is the mean of its key's vertices
+    for (int64_t i = 0; i < c.ndofs; ++i)
+      for (int d = 0; d < 3; ++d) {
+        double s = 0.0;
+        for (int r = 0; r < c.p; ++r) s += c.xyz[3 * size_t(c.dof_keys[size_t(i) * c.p + r]) + d];
+        xyz[3 * i + d] = s / c.p;
+      }
+    return FEM_OK;
+  }
+  // DG: library DoF e * nd + j is node beta_j of library cell e: sum_a beta_j[a] x_a / p
+  std::vector<std::array<int, 4>> betas;
+  for (int b0 = 0; b0 <= c.p; ++b0)
+    for (int b1 = 0; b1 <= c.p - b0; ++b1)
+      for (int b2 = 0; b2 <= c.p - b0 - b1; ++b2) betas.push_back({b0, b1, b2, c.p - b0 - b1 - b2});
+  for (int64_t e = 0; e < c.nc; ++e) {
+    const int32_t* cv = c.ucells.data() + 4 * size_t(c.cell_perm[e]);
+    for (int j = 0; j < c.nd; ++j)
+      for (int d = 0; d < 3; ++d) {
+        double s = 0.0;
+        for (int a = 0; a < 4; ++a) s += betas[j][a] * c.xyz[3 * size_t(cv[a]) + d];
+        xyz[3 * (e * c.nd + j) + d] = s / c.p;
+      }
+  }
   return FEM_OK;
 }
 

@@ -92,6 +92,12 @@ class FemSpace:
         call("fem_dof_keys", self._h, out.ctypes.data)
         return out
 
+    def dof_coordinates(self):
+        """Node positions of the library DoFs, [N, 3] float64 (host)."""
+        out = np.empty((self.n_dofs, 3), dtype=np.float64)
+        call("fem_dof_coordinates", self._h, out.ctypes.data)
+        return out
+
     def dirichlet_mask(self):
         out = np.empty(self.n_dofs, dtype=np.uint8)
         call("fem_dirichlet_mask", self._h, out.ctypes.data)

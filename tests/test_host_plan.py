@@ -58,6 +58,30 @@ def test_dg_numbering_and_faces():
     assert sp.n_boundary_faces == boundary.shape[0]
 
 
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_dof_coordinates(p):
+    """CG: on the unjittered Kuhn cube the nodes are exactly the (p n + 1)^3 lattice (each once);
+    on a jittered, shuffled mesh each node is the mean of its key's vertices.  DG: the nodes of
+    each cell are its barycentric points beta / p in the user's vertex order."""
+    from oracle import basis
+
+    n = 3
+    xyz, cells = synth.kuhn_cube(n, jitter=0.0, seed=0)
+    X = space(xyz, cells, degree=p).dof_coordinates()
+    lat = np.rint(X * p * n)
+    assert np.abs(X * p * n - lat).max() < 1e-9
+    codes = (lat[:, 0] * (p * n + 1) + lat[:, 1]) * (p * n + 1) + lat[:, 2]
+    assert np.array_equal(np.sort(codes), np.arange((p * n + 1) ** 3))
+    xyz, cells = synth.kuhn_cube(n, jitter=0.2, seed=2)
+    xyz, cells, _ = synth.shuffle_mesh(xyz, cells, seed=4)
+    sp = space(xyz, cells, degree=p)
+    assert np.allclose(sp.dof_coordinates(), xyz[sp.dof_keys()].mean(axis=1), rtol=0, atol=1e-14)
+    sp = space(xyz, cells, kind="dg", degree=p)
+    nodes = np.array(basis.nodes_beta(p), dtype=np.float64) / p
+    expect = np.einsum("nk,ckd->cnd", nodes, xyz[cells[sp.cell_permutation()]]).reshape(-1, 3)
+    assert np.allclose(sp.dof_coordinates(), expect, rtol=0, atol=1e-14)
+
+
 def test_morton_reorder_improves_locality():
     """Reordering a shuffled mesh makes the cells of a 128-cell batch share vertices (Sec. 2.5)."""
     xyz, cells = synth.kuhn_cube(8, jitter=0.2, seed=0)
