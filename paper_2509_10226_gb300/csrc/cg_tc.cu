@@ -6,8 +6,10 @@
 // cells to 128 cells = the M of one tcgen05.mma):
 //   GEMM 1:  G[128 x 3nq]  = U'[128 x nd-1] . E'^T   (E' = columns 1..nd-1 of E, Eq. 4;
 //                                                     U'[m, j-1] = u_j - u_0 of cell m)
-//   D_e:     Q[m, 3q+k]    = w_q k_q (M_e G[m, 3q:3q+3])_k    per thread (row m)
+//   D_e:     Q[m, (q,k)]   = w_q k_q (M_e G[m, (q,0..2)])_k  per thread (row m)
 //   GEMM 2:  Y'[128 x nd-1] = Q[128 x 3nq] . E',      y_0 = -sum_{j>=1} y_j
+// Columns (q, k) of G and Q are stored in pairs of points, (x_q, x_q', y_q, y_q', z_q, z_q'),
+// so that the metric step runs on packed FP32x2 instructions (grad_col).
 // The difference form is E u_e rewritten with sum_j E_j = 0 (partition of
 // unity); it is exact for exact tables and keeps rounded TF32/BF16 tables
 // consistent (constants map to zero, operand error relative to the gradient).
@@ -360,14 +362,16 @@ std::vector<uint8_t> b_image(const RefTables& t) {
   auto off = [](int r, int k, int lbo) {
     return size_t((k / S::KC) * lbo + (r / 8) * 128 + (r % 8) * 16 + (k % S::KC) * S::ES);
   };
-  // B1 = E' as [N1 rows = 3q+k][K1 = j-1]; B2 = (w E')^T as [N2 rows = j-1][K2 = 3q+k]
+  // B1 = E' as [N1 rows = grad_col(q, k)][K1 = j-1]; B2 = (w E')^T as [N2 rows = j-1][K2 = grad_col(q, k)]
   // (the quadrature weight w_q is folded into the integration table)
-  for (int n = 0; n < S::N3; ++n)
-    for (int j = 1; j < ND; ++j) {
-      const double e = t.E[size_t(n) * ND + j];
-      put_elem<BF16>(img, off(n, j - 1, S::LBO_B1), e);
-      put_elem<BF16>(img, S::B1_BYTES + off(j - 1, n, S::LBO_B2), e * t.wq[n / 3]);
-    }
+  for (int q = 0; q < NQ; ++q)
+    for (int k = 0; k < 3; ++k)
+      for (int j = 1; j < ND; ++j) {
+        const double e = t.E[(size_t(q) * 3 + k) * ND + j];
+        const int n = grad_col(q, k);
+        put_elem<BF16>(img, off(n, j - 1, S::LBO_B1), e);
+        put_elem<BF16>(img, S::B1_BYTES + off(j - 1, n, S::LBO_B2), e * t.wq[q]);
+      }
   return img;
 }
 

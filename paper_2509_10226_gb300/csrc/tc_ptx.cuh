@@ -172,20 +172,49 @@ __device__ __forceinline__ bool wg_any(int g, bool v) {
   return r != 0;
 }
 
+// Column order of the gradients G (GEMM 1 output) and of Q (GEMM 2 K index): quadrature points
+// in pairs (q, q') = (2 p, 2 p + 1), six columns per pair, (x_q, x_q', y_q, y_q', z_q, z_q'), so
+// that one packed FP32x2 instruction applies the metric to two points; an odd count leaves the
+// last pair's second point as zero padding (zero table rows).
+__host__ __device__ constexpr int grad_col(int q, int k) { return 6 * (q / 2) + 2 * k + (q % 2); }
+
+// (x, x', y, y', z, z') <- M (x, y, z) for two points at once: t_x = m0 x + m1 y + m2 z,
+// t_y = m1 x + m3 y + m4 z, t_z = m2 x + m4 y + m5 z (same rounding as the scalar fmaf chain);
+// M0..M5 hold each metric entry in both halves
+__device__ __forceinline__ void metric_pair(uint32_t* d, uint64_t M0, uint64_t M1, uint64_t M2, uint64_t M3,
+                                            uint64_t M4, uint64_t M5) {
+  asm("{\n\t.reg .b64 gx, gy, gz, tx, ty, tz;\n\t"
+      "mov.b64 gx, {%0, %1};\n\tmov.b64 gy, {%2, %3};\n\tmov.b64 gz, {%4, %5};\n\t"
+      "mul.rn.f32x2 tx, %8, gz;\n\tfma.rn.f32x2 tx, %7, gy, tx;\n\tfma.rn.f32x2 tx, %6, gx, tx;\n\t"
+      "mul.rn.f32x2 ty, %10, gz;\n\tfma.rn.f32x2 ty, %9, gy, ty;\n\tfma.rn.f32x2 ty, %7, gx, ty;\n\t"
+      "mul.rn.f32x2 tz, %11, gz;\n\tfma.rn.f32x2 tz, %10, gy, tz;\n\tfma.rn.f32x2 tz, %8, gx, tz;\n\t"
+      "mov.b64 {%0, %1}, tx;\n\tmov.b64 {%2, %3}, ty;\n\tmov.b64 {%4, %5}, tz;\n\t}"
+      : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3]), "+r"(d[4]), "+r"(d[5])
+      : "l"(M0), "l"(M1), "l"(M2), "l"(M3), "l"(M4), "l"(M5));
+}
+__device__ __forceinline__ uint64_t splat2(float v) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "r"(__float_as_uint(v)));
+  return r;
+}
+
 // D_e of Eq. 3 for one cell (row m = the thread's TMEM lane): the reference gradients G in
-// TMEM columns [0, 3 NQ) are replaced in place by Q = (k_q) M_e g_q, in chunks of 16 points
-// (48 columns); columns past 3 NQ in the last chunk are zeroed.  TF32: FP32 bits, one column
-// per element; BF16: pairs packed into one column (Q column e / 2), which never overtakes the
-// columns still to be read.  kq = this cell's coefficients at the NQ points, or null.
+// TMEM (columns in grad_col order) are replaced in place by Q = (k_q) M_e g_q, in chunks of 16
+// points (8 pairs, 48 columns); columns past the last pair in the last chunk are zeroed.
+// TF32: FP32 bits, one column per element; BF16: pairs packed into one column (Q column e / 2),
+// which never overtakes the columns still to be read.  kq = this cell's coefficients at the NQ
+// points, or null.
 template <int ND, int NQ, bool BF16, bool HAS_K>
 __device__ __forceinline__ void metric_to_q(uint32_t lane_base, float m0, float m1, float m2, float m3, float m4,
                                             float m5, const float* kq) {
-  constexpr int NCHUNK = (NQ + 15) / 16;
+  constexpr int NP = (NQ + 1) / 2;  // point pairs
+  constexpr int NCHUNK = (NP + 7) / 8;
+  const uint64_t M0 = splat2(m0), M1 = splat2(m1), M2 = splat2(m2), M3 = splat2(m3), M4 = splat2(m4),
+                 M5 = splat2(m5);
 #pragma unroll
   for (int c = 0; c < NCHUNK; ++c) {
-    const int q0 = 16 * c;
-    const int nq = (NQ - q0) < 16 ? (NQ - q0) : 16;
-    const int nl = (3 * nq + 15) / 16;  // x16 loads in this chunk
+    const int np = (NP - 8 * c) < 8 ? (NP - 8 * c) : 8;  // pairs in this chunk
+    const int nl = (6 * np + 15) / 16;                    // x16 loads in this chunk
     uint32_t d[48];
 #pragma unroll
     for (int l = 0; l < 3; ++l)
@@ -195,26 +224,22 @@ __device__ __forceinline__ void metric_to_q(uint32_t lane_base, float m0, float 
     for (int l = 0; l < 3; ++l)
       if (l < nl) reg_fence16(d + 16 * l);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      if (i < nq) {
-        const float gx = __uint_as_float(d[3 * i]), gy = __uint_as_float(d[3 * i + 1]),
-                    gz = __uint_as_float(d[3 * i + 2]);
-        float tx = fmaf(m0, gx, fmaf(m1, gy, m2 * gz));
-        float ty = fmaf(m1, gx, fmaf(m3, gy, m4 * gz));
-        float tz = fmaf(m2, gx, fmaf(m4, gy, m5 * gz));
+    for (int i = 0; i < 8; ++i) {
+      if (i < np) {
+        metric_pair(d + 6 * i, M0, M1, M2, M3, M4, M5);
         if constexpr (HAS_K) {
-          const float k = kq[q0 + i];
-          tx *= k;
-          ty *= k;
-          tz *= k;
+          const int q = 16 * c + 2 * i;
+          const float k0 = kq[q], k1 = q + 1 < NQ ? kq[q + 1] : 0.0f;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            d[6 * i + 2 * a] = __float_as_uint(__uint_as_float(d[6 * i + 2 * a]) * k0);
+            d[6 * i + 2 * a + 1] = __float_as_uint(__uint_as_float(d[6 * i + 2 * a + 1]) * k1);
+          }
         }
-        d[3 * i] = __float_as_uint(tx);
-        d[3 * i + 1] = __float_as_uint(ty);
-        d[3 * i + 2] = __float_as_uint(tz);
-      } else if (3 * i < 16 * nl) {
-        d[3 * i] = 0u;
-        if (3 * i + 1 < 16 * nl) d[3 * i + 1] = 0u;
-        if (3 * i + 2 < 16 * nl) d[3 * i + 2] = 0u;
+      } else {
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+          if (6 * i + a < 16 * nl) d[6 * i + a] = 0u;
       }
     }
     if constexpr (BF16) {
@@ -256,7 +281,7 @@ struct TcShape {
   static constexpr int ES = BF16 ? 2 : 4;
   static constexpr int KC = 16 / ES;
   static constexpr int KSTEP = 2 * KC;
-  static constexpr int N3 = 3 * NQ;
+  static constexpr int N3 = 6 * ((NQ + 1) / 2);  // gradient columns in grad_col order (pairs of points)
   static constexpr int ND1 = ND - 1;  // DoFs 1..nd-1 enter as differences to DoF 0
   static constexpr int K1 = round_up(ND1, KSTEP);
   static constexpr int N1 = round_up(N3, 16);
@@ -267,7 +292,6 @@ struct TcShape {
   static constexpr int QW = BF16 ? N1 / 2 : N1;
   static constexpr int D2_COL = N1;  // Y' is read while GEMM 1 of the next tile writes G
   static constexpr int COLS = pow2_cols(N1 + N2);
-  static constexpr int NCHUNK = (NQ + 15) / 16;  // epilogue chunks of 16 points (48 columns)
   static constexpr int LBO_A = (kTile / 8) * 128;
   static constexpr int LBO_B1 = (N1 / 8) * 128;
   static constexpr int LBO_B2 = (N2 / 8) * 128;
