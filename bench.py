@@ -176,6 +176,11 @@ def time_steps(torch, fn, steps, warmup, flush, stream, barrier):
     return [a.elapsed_time(b) for a, b in ev]
 
 
+def tstat(ms):
+    """Median and minimum of per-step times (ms), next to the mean each line reports."""
+    return {"ms_median": float(np.median(ms)), "ms_min": float(np.min(ms))}
+
+
 def oracle_cpu_baseline(xyz, cells, p, N, target_s=10.0):
     """The FP64 oracle (plain numpy cell loop, single thread) on a bounded sample of the same mesh; returns
     its throughput scaled to whole-problem DoFs: (sample cells / s) x (N / C)."""
@@ -366,7 +371,7 @@ def main():
 
         t = float(np.mean(ms64))
         fl = cg_flops(C, nd, nq)
-        variants["fp64"] = {"gdofs": N / (t * 1e-3) / 1e9, "ms": t, "bound": "alu",
+        variants["fp64"] = {**tstat(ms64), "gdofs": N / (t * 1e-3) / 1e9, "ms": t, "bound": "alu",
                             "achieved_tflops": fl / (t * 1e-3) / 1e12, "peak_tflops": NOMINAL_FP64_TFLOPS,
                             "frac": fl / (t * 1e-3) / 1e12 / NOMINAL_FP64_TFLOPS, "flops_counted": "Eq. 6",
                             "hbm_gbs": cg_bytes(C, N, nd, "fp64") / (t * 1e-3) / 1e9}
@@ -374,13 +379,13 @@ def main():
             msv = time_steps(torch, lambda: sp.apply(u32, prec=prec, out=y32), vsteps, 2, flush, stream, barrier)
             t = float(np.mean(msv))
             gbs = cg_bytes(C, N, nd, prec) / (t * 1e-3) / 1e9
-            variants[prec] = {"gdofs": N / (t * 1e-3) / 1e9, "ms": t, "hbm_gbs": gbs,
+            variants[prec] = {**tstat(msv), "gdofs": N / (t * 1e-3) / 1e9, "ms": t, "hbm_gbs": gbs,
                               "frac_hbm": gbs / peaks["hbm_gbs"], "rel_l2_vs_fp64": rel(y32)}
             if prec == "fp32":
                 fmax = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
                 variants[prec].update({"bound": "alu", "achieved_tflops": fl / (t * 1e-3) / 1e12,
                                        "peak_tflops_fp32_fma": fmax})
-        variants["tf32"] = {"gdofs": value / world, "ms": t_head, "hbm_gbs": achieved,
+        variants["tf32"] = {**tstat(ms), "gdofs": value / world, "ms": t_head, "hbm_gbs": achieved,
                             "frac_hbm": achieved / peaks["hbm_gbs"], "rel_l2_vs_fp64": rel(y_head)}
         if not args.no_csr:
             try:
@@ -394,7 +399,7 @@ def main():
                     vb = 8 if prec == "fp64" else 4
                     b = nnz * (4 + vb) + 8 * (N + 1) + 2 * vb * N
                     gbs = b / (t * 1e-3) / 1e9
-                    variants[f"csr_{prec}"] = {"gdofs": N / (t * 1e-3) / 1e9, "ms": t, "nnz": nnz,
+                    variants[f"csr_{prec}"] = {**tstat(msv), "gdofs": N / (t * 1e-3) / 1e9, "ms": t, "nnz": nnz,
                                                "hbm_gbs": gbs, "frac_hbm": gbs / peaks["hbm_gbs"],
                                                "rel_l2_vs_fp64": rel(y_), "build_s": build_s}
             except Exception as e:  # noqa: BLE001
@@ -413,7 +418,7 @@ def main():
                         msv = time_steps(torch, lambda: ssp.apply(su, prec=prec, out=sy), vsteps, 2, flush, stream,
                                          barrier)
                         t = float(np.mean(msv))
-                        variants[f"shuffled_reorder_{tag}_{prec}"] = {"gdofs": ssp.n_dofs / (t * 1e-3) / 1e9, "ms": t}
+                        variants[f"shuffled_reorder_{tag}_{prec}"] = {**tstat(msv), "gdofs": ssp.n_dofs / (t * 1e-3) / 1e9, "ms": t}
                     del ssp, su, sy
             except Exception as e:  # noqa: BLE001
                 variants["shuffled_reorder"] = {"unavailable": str(e).splitlines()[0]}
@@ -437,7 +442,7 @@ def main():
                                      barrier)
                     t = float(np.mean(msv))
                     b = dg_bytes(dsp.n_cells, dsp.n_interior_faces, dsp.n_boundary_faces, 10, prec)
-                    variants[f"dg_p2_48_{prec}"] = {"gdofs": dsp.n_dofs / (t * 1e-3) / 1e9, "ms": t,
+                    variants[f"dg_p2_48_{prec}"] = {**tstat(msv), "gdofs": dsp.n_dofs / (t * 1e-3) / 1e9, "ms": t,
                                                     "n_dofs": dsp.n_dofs, "hbm_gbs": b / (t * 1e-3) / 1e9}
                 for prec, y_ in (("fp32", dy32), ("tf32", dytc["tf32"]), ("bf16", dytc["bf16"])):
                     variants[f"dg_p2_48_{prec}"]["rel_l2_vs_fp64"] = float(
@@ -455,8 +460,8 @@ def main():
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_head, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "tf32", "data": "synthetic",
+            "warmup": args.warmup, "ms_per_step": t_head, **tstat(ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "tf32", "data": "synthetic",
             "config": {"workload": f"CG P3 Laplacian, {n}^3 Kuhn cube ({C:,} tets, {N:,} DoFs), jitter 0.2h, "
                                    f"Morton order, u ~ U[-1,1]; TF32 tensor-core apply, FP32 vectors",
                        "cells": C, "dofs": N, "degree": p, "quadrature": "Grundmann-Moeller s=3 (35 points)",
