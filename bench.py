@@ -214,7 +214,8 @@ def time_solves(torch, FemSpace, device):
     b = sp.rhs_const(1.0)
     sp.solve(b, mode="ir", inner_prec="tf32", rtol=1e-3, raise_on_notconv=False)
     out = {"n_dofs": sp.n_dofs, "rtol": 1e-10}
-    for name, mode, inner in (("ir_tf32", "ir", "tf32"), ("ir_bf16", "ir", "bf16"), ("ir_fp32", "ir", "fp32"),
+    for name, mode, inner in (("ir_tf32", "ir", "tf32"), ("ir_bf16", "ir", "bf16"), ("ir_tf32x3", "ir", "tf32x3"),
+                              ("ir_fp32", "ir", "fp32"),
                               ("pcg_fp64", "pcg", "fp32")):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -375,7 +376,7 @@ def main():
                             "achieved_tflops": fl / (t * 1e-3) / 1e12, "peak_tflops": NOMINAL_FP64_TFLOPS,
                             "frac": fl / (t * 1e-3) / 1e12 / NOMINAL_FP64_TFLOPS, "flops_counted": "Eq. 6",
                             "hbm_gbs": cg_bytes(C, N, nd, "fp64") / (t * 1e-3) / 1e9}
-        for prec in ("fp32", "bf16"):
+        for prec in ("fp32", "bf16", "tf32x3"):
             msv = time_steps(torch, lambda: sp.apply(u32, prec=prec, out=y32), vsteps, 2, flush, stream, barrier)
             t = float(np.mean(msv))
             gbs = cg_bytes(C, N, nd, prec) / (t * 1e-3) / 1e9

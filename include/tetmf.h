@@ -73,6 +73,10 @@ extern "C" {
 #define FEM_FP32 1   /* FP32 FMA units                                      */
 #define FEM_TF32 2   /* tcgen05 tensor cores, TF32 operands, FP32 accumulate */
 #define FEM_BF16 3   /* tcgen05 tensor cores, BF16 operands, FP32 accumulate */
+#define FEM_TF32X3 4 /* tcgen05 tensor cores, 3xTF32: every operand split into */
+                     /* a TF32 high part and a TF32 low part, products       */
+                     /* hi*hi + hi*lo + lo*hi accumulated in FP32 (CG,      */
+                     /* degrees 1-3)                                        */
 
 #define FEM_REORDER_NONE 0
 #define FEM_REORDER_MORTON 1
@@ -190,7 +194,7 @@ int fem_csr_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, void* stre
 /* ---- solve (blocking) ---------------------------------------------- */
 typedef struct {
   int32_t mode;          /* FEM_SOLVE_FP64_PCG or FEM_SOLVE_IR_MIXED         */
-  int32_t inner_prec;    /* IR: FEM_FP32, FEM_TF32 or FEM_BF16 inner apply   */
+  int32_t inner_prec;    /* IR: FEM_FP32, FEM_TF32, FEM_BF16 or FEM_TF32X3    */
   double rtol;           /* stop when ||b - A x|| / ||b|| <= rtol (FP64)     */
   double inner_rtol;     /* IR: relative reduction asked of each inner solve */
   int32_t max_outer;     /* IR outer iterations cap                          */

@@ -15,7 +15,7 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "tetmf.h")
 
 FEM_OK, FEM_EINVAL, FEM_EMESH, FEM_EUNSUPPORTED, FEM_ECUDA, FEM_ENOTCONV, FEM_ENOMEM = range(7)
 FEM_CG, FEM_DG = 0, 1
-FEM_FP64, FEM_FP32, FEM_TF32, FEM_BF16 = 0, 1, 2, 3
+FEM_FP64, FEM_FP32, FEM_TF32, FEM_BF16, FEM_TF32X3 = 0, 1, 2, 3, 4
 FEM_REORDER_NONE, FEM_REORDER_MORTON = 0, 1
 FEM_SOLVE_FP64_PCG, FEM_SOLVE_IR_MIXED = 0, 1
 

@@ -123,18 +123,20 @@ __device__ inline void issue_gather(const Stage<ND, NQ, HAS_K>& st, int m, int L
 // One CTA = G warpgroups of 128 threads; each warpgroup runs the tile loop on
 // its own tiles with its own operand buffer, stages, mbarrier and TMEM
 // columns (TCOLS each), sharing the E tables.  G is blockDim.x / 128.
-template <int ND, int NQ, bool BF16>
+// X3 (3xTF32) adds the low parts of Q after Y' in TMEM and a second (low-part) image of each
+// table and a second A operand in shared memory.
+template <int ND, int NQ, bool BF16, bool X3>
 constexpr int tc_tcols() {
   using S = TcShape<ND, NQ, BF16>;
-  return round_up(S::D2_COL + S::N2, 16);
+  return X3 ? round_up(2 * S::N1 + S::N2, 16) : round_up(S::D2_COL + S::N2, 16);
 }
-template <int ND, int NQ, bool BF16>
+template <int ND, int NQ, bool BF16, bool X3>
 constexpr int tc_max_groups() {
-  return 512 / tc_tcols<ND, NQ, BF16>() < 4 ? 512 / tc_tcols<ND, NQ, BF16>() : 4;
+  return 512 / tc_tcols<ND, NQ, BF16, X3>() < 4 ? 512 / tc_tcols<ND, NQ, BF16, X3>() : 4;
 }
 
-template <int ND, int NQ, bool BF16, bool HAS_K>
-__global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
+template <int ND, int NQ, bool BF16, bool HAS_K, bool X3>
+__global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3>(), 1)
     k_cg_apply_tc(const int64_t* __restrict__ tl_span, const int32_t* __restrict__ tl_list,
                   const uint16_t* __restrict__ tl_lidx, const float* __restrict__ metric,
                   const uint8_t* __restrict__ bimg, const float* __restrict__ u, float* __restrict__ y,
@@ -142,18 +144,22 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
                   int32_t* __restrict__ status) {
   using S = TcShape<ND, NQ, BF16>;
   using St = Stage<ND, NQ, HAS_K>;
+  static_assert(!(X3 && BF16), "3xTF32 splits TF32 operands");
   constexpr int KS = NQ | 1;
   constexpr int NDP = round_up(ND, 2);
-  constexpr int TCOLS = round_up(S::D2_COL + S::N2, 16);
+  constexpr int TCOLS = tc_tcols<ND, NQ, BF16, X3>();
+  constexpr int NIMG = X3 ? 2 : 1;            // high (and low) parts of the tables and of U'
+  constexpr int QLO = S::N1 + S::N2;          // X3: TMEM columns of the low part of Q
+  constexpr int IMG_BYTES = S::B1_BYTES + S::B2_BYTES;
   extern __shared__ __align__(1024) uint8_t smem[];
   const int G = blockDim.x / kT;
   const int g = threadIdx.x / kT;   // warpgroup
   const int m = threadIdx.x % kT;   // row of the tile = TMEM lane
   const int warp = threadIdx.x >> 5;
-  uint8_t* sB1 = smem;
+  uint8_t* sB1 = smem;                        // [B1 | B2] high parts, then [B1 | B2] low parts (X3)
   uint8_t* sB2 = sB1 + S::B1_BYTES;
-  uint8_t* sA1 = sB2 + S::B2_BYTES + size_t(g) * S::A1_BYTES;
-  uint8_t* misc = sB2 + S::B2_BYTES + size_t(G) * S::A1_BYTES;  // [G][32]: mbarrier, TMEM slot
+  uint8_t* sA1 = smem + NIMG * IMG_BYTES + size_t(g) * NIMG * S::A1_BYTES;
+  uint8_t* misc = smem + NIMG * IMG_BYTES + size_t(G) * NIMG * S::A1_BYTES;  // [G][32]: mbarrier, TMEM slot
   uint64_t* bar = reinterpret_cast<uint64_t*>(misc + 32 * g);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 8);       // warpgroup 0's slot
   uint32_t* wmax = reinterpret_cast<uint32_t*>(misc + 32 * g + 16);  // per-warp maxima
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
   {
     const uint4* src = reinterpret_cast<const uint4*>(bimg);
     uint4* dst = reinterpret_cast<uint4*>(sB1);
-    for (int i = threadIdx.x; i < (S::B1_BYTES + S::B2_BYTES) / 16; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < NIMG * IMG_BYTES / 16; i += blockDim.x) dst[i] = src[i];
   }
   const uint32_t bar_a = smem_u32(bar);
   if (m == 0) mbar_init(bar_a);
@@ -280,6 +286,16 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
       for (int j = 1; j < ND; ++j) v1[j - 1] = cur.vals[pos(j)] - ue0;
 #pragma unroll
       for (int j = S::ND1; j < S::K1; ++j) v1[j] = 0.0f;
+      if constexpr (X3) {
+        float lo[S::K1];
+#pragma unroll
+        for (int j = 0; j < S::K1; ++j) {
+          const float h = __uint_as_float(tf32_hi(__float_as_uint(v1[j])));
+          lo[j] = v1[j] - h;
+          v1[j] = h;
+        }
+        write_row<S::K1, false>(sA1 + S::A1_BYTES, m, lo);
+      }
       write_row<S::K1, BF16>(sA1, m, v1);
     }
     fence_proxy_async();
@@ -293,9 +309,19 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
     // 2. GEMM 1 of tile t; meanwhile clear tile t's accumulator and scatter tile t-1
     if (m == 0) {
 #pragma unroll
-      for (int s = 0; s < S::K1 / S::KSTEP; ++s)
-        mma<BF16>(tmem, smem_desc(aA1 + s * 2 * S::LBO_A, S::LBO_A, 128),
-                  smem_desc(aB1 + s * 2 * S::LBO_B1, S::LBO_B1, 128), S::idesc(S::N1), s > 0);
+      for (int s = 0; s < S::K1 / S::KSTEP; ++s) {
+        const uint64_t a_hi = smem_desc(aA1 + s * 2 * S::LBO_A, S::LBO_A, 128);
+        const uint64_t b_hi = smem_desc(aB1 + s * 2 * S::LBO_B1, S::LBO_B1, 128);
+        if constexpr (X3) {
+          // small products first: A_lo B_hi + A_hi B_lo, then A_hi B_hi
+          mma<BF16>(tmem, smem_desc(aA1 + S::A1_BYTES + s * 2 * S::LBO_A, S::LBO_A, 128), b_hi, S::idesc(S::N1),
+                    s > 0);
+          mma<BF16>(tmem, a_hi, smem_desc(aB1 + IMG_BYTES + s * 2 * S::LBO_B1, S::LBO_B1, 128), S::idesc(S::N1), 1);
+          mma<BF16>(tmem, a_hi, b_hi, S::idesc(S::N1), 1);
+        } else {
+          mma<BF16>(tmem, a_hi, b_hi, S::idesc(S::N1), s > 0);
+        }
+      }
       mma_commit(bar_a);
     }
     for (int i = m; i < (L + 4) / 4; i += kT) reinterpret_cast<float4*>(cur.vals)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -316,7 +342,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
     else
       cp_async_commit();
     // 3. D_e per quadrature point: G in TMEM becomes Q = (k_q) M_e g_q (w_q is folded into the table of GEMM 2)
-    metric_to_q<ND, NQ, BF16, HAS_K>(lane_base, m0, m1, m2, m3, m4, m5, HAS_K ? cur.kt + m * KS : nullptr);
+    metric_to_q<ND, NQ, BF16, HAS_K, X3>(lane_base, m0, m1, m2, m3, m4, m5, HAS_K ? cur.kt + m * KS : nullptr, QLO);
     tmem_wait_st();
     tc_fence_before();
     wg_sync(g);
@@ -324,9 +350,17 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
     if (m == 0) {
       tc_fence_after();
 #pragma unroll
-      for (int s = 0; s < S::K2 / S::KSTEP; ++s)
-        mma_ta<BF16>(tmem + S::D2_COL, tmem + 8 * s, smem_desc(aB2 + s * 2 * S::LBO_B2, S::LBO_B2, 128),
-                     S::idesc(S::N2), s > 0);
+      for (int s = 0; s < S::K2 / S::KSTEP; ++s) {
+        const uint64_t b_hi = smem_desc(aB2 + s * 2 * S::LBO_B2, S::LBO_B2, 128);
+        if constexpr (X3) {
+          mma_ta<BF16>(tmem + S::D2_COL, tmem + QLO + 8 * s, b_hi, S::idesc(S::N2), s > 0);
+          mma_ta<BF16>(tmem + S::D2_COL, tmem + 8 * s, smem_desc(aB2 + IMG_BYTES + s * 2 * S::LBO_B2, S::LBO_B2, 128),
+                       S::idesc(S::N2), 1);
+          mma_ta<BF16>(tmem + S::D2_COL, tmem + 8 * s, b_hi, S::idesc(S::N2), 1);
+        } else {
+          mma_ta<BF16>(tmem + S::D2_COL, tmem + 8 * s, b_hi, S::idesc(S::N2), s > 0);
+        }
+      }
       mma_commit(bar_a);
     }
     cp_async_wait_group<1>();  // gather of tile t+1 (this thread's share; published by the next barrier)
@@ -355,10 +389,22 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16>(), 1)
   if (failed && m == 0) atomicOr(status, 1);
 }
 
-template <int ND, int NQ, bool BF16>
+// TF32 value of v as the image stores it (round to nearest, ties away from zero)
+double tf32_value(double v) {
+  float f = float(v);
+  uint32_t bits;
+  std::memcpy(&bits, &f, 4);
+  bits = (bits + 0x1000u) & 0xFFFFE000u;
+  std::memcpy(&f, &bits, 4);
+  return double(f);
+}
+
+// Operand images of the two tables; X3: the TF32 high parts, then the low parts (table - high part)
+template <int ND, int NQ, bool BF16, bool X3>
 std::vector<uint8_t> b_image(const RefTables& t) {
   using S = TcShape<ND, NQ, BF16>;
-  std::vector<uint8_t> img(S::B1_BYTES + S::B2_BYTES, 0);
+  constexpr size_t IMG = S::B1_BYTES + S::B2_BYTES;
+  std::vector<uint8_t> img((X3 ? 2 : 1) * IMG, 0);
   auto off = [](int r, int k, int lbo) {
     return size_t((k / S::KC) * lbo + (r / 8) * 128 + (r % 8) * 16 + (k % S::KC) * S::ES);
   };
@@ -368,23 +414,29 @@ std::vector<uint8_t> b_image(const RefTables& t) {
     for (int k = 0; k < 3; ++k)
       for (int j = 1; j < ND; ++j) {
         const double e = t.E[(size_t(q) * 3 + k) * ND + j];
+        const double ew = e * t.wq[q];
         const int n = grad_col(q, k);
         put_elem<BF16>(img, off(n, j - 1, S::LBO_B1), e);
-        put_elem<BF16>(img, S::B1_BYTES + off(j - 1, n, S::LBO_B2), e * t.wq[q]);
+        put_elem<BF16>(img, S::B1_BYTES + off(j - 1, n, S::LBO_B2), ew);
+        if (X3) {
+          put_elem<false>(img, IMG + off(n, j - 1, S::LBO_B1), e - tf32_value(e));
+          put_elem<false>(img, IMG + S::B1_BYTES + off(j - 1, n, S::LBO_B2), ew - tf32_value(ew));
+        }
       }
   return img;
 }
 
-template <int ND, int NQ, bool BF16, bool HAS_K>
+template <int ND, int NQ, bool BF16, bool HAS_K, bool X3>
 size_t tc_smem(int lmax, int G) {
   using S = TcShape<ND, NQ, BF16>;
-  return size_t(S::B1_BYTES) + S::B2_BYTES +
-         size_t(G) * (S::A1_BYTES + 32 + kStages * stage_bytes<ND, NQ, HAS_K>(lmax));
+  constexpr int NIMG = X3 ? 2 : 1;
+  return size_t(NIMG) * (S::B1_BYTES + S::B2_BYTES) +
+         size_t(G) * (NIMG * S::A1_BYTES + 32 + kStages * stage_bytes<ND, NQ, HAS_K>(lmax));
 }
 
-template <int ND, int NQ, bool BF16>
+template <int ND, int NQ, bool BF16, bool X3>
 int upload_image(Ctx& c, void** dst) {
-  const std::vector<uint8_t> img = b_image<ND, NQ, BF16>(c.tab);
+  const std::vector<uint8_t> img = b_image<ND, NQ, BF16, X3>(c.tab);
   void* p = nullptr;
   TETMF_CK(cudaMalloc(&p, img.size()));
   c.allocations.push_back(p);
@@ -395,23 +447,23 @@ int upload_image(Ctx& c, void** dst) {
 
 template <int ND, int NQ>
 int prepare(Ctx& c) {
-  if (int s = upload_image<ND, NQ, false>(c, &c.d_tc_tf32)) return s;
-  return upload_image<ND, NQ, true>(c, &c.d_tc_bf16);
+  if (int s = upload_image<ND, NQ, false, false>(c, &c.d_tc_tf32)) return s;
+  if (int s = upload_image<ND, NQ, false, true>(c, &c.d_tc_tf32x3)) return s;
+  return upload_image<ND, NQ, true, false>(c, &c.d_tc_bf16);
 }
 
-template <int ND, int NQ, bool BF16, bool HAS_K>
+template <int ND, int NQ, bool BF16, bool HAS_K, bool X3>
 int launch_g(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) {
-  using S = TcShape<ND, NQ, BF16>;
-  constexpr int TCOLS = round_up(S::D2_COL + S::N2, 16);
+  constexpr int TCOLS = tc_tcols<ND, NQ, BF16, X3>();
   const int lmax = round_up(c.tl_max + 1, 4);  // list + the zero slot
-  auto kern = k_cg_apply_tc<ND, NQ, BF16, HAS_K>;
+  auto kern = k_cg_apply_tc<ND, NQ, BF16, HAS_K, X3>;
   int dev = 0, smem_max = 0;
   TETMF_CK(cudaGetDevice(&dev));
   TETMF_CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   // warpgroups per CTA: as many tiles in flight per SM as TMEM (512 columns) and shared memory allow
-  int G = tc_max_groups<ND, NQ, BF16>();
-  while (G > 1 && tc_smem<ND, NQ, BF16, HAS_K>(lmax, G) > size_t(smem_max)) --G;
-  const size_t sm = tc_smem<ND, NQ, BF16, HAS_K>(lmax, G);
+  int G = tc_max_groups<ND, NQ, BF16, X3>();
+  while (G > 1 && tc_smem<ND, NQ, BF16, HAS_K, X3>(lmax, G) > size_t(smem_max)) --G;
+  const size_t sm = tc_smem<ND, NQ, BF16, HAS_K, X3>(lmax, G);
   if (G < 1 || sm > size_t(smem_max)) {
     set_error("tensor-core kernel does not fit on an SM (%zu bytes of shared memory)", sm);
     return FEM_EUNSUPPORTED;
@@ -420,17 +472,33 @@ int launch_g(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) 
   const uint32_t cols = uint32_t(pow2_cols(G * TCOLS));
   int64_t grid = (c.ntiles + G - 1) / G;
   if (grid > sm_count()) grid = sm_count();
+  const void* img = X3 ? c.d_tc_tf32x3 : BF16 ? c.d_tc_bf16 : c.d_tc_tf32;
   kern<<<unsigned(grid), G * kT, sm, st>>>(c.d_tl_span, c.d_tl_list, c.d_tl_lidx, c.d_metric32,
-                                           static_cast<const uint8_t*>(BF16 ? c.d_tc_bf16 : c.d_tc_tf32), u, y, k,
-                                           c.nc, c.ntiles, lmax, cols, c.d_status);
+                                           static_cast<const uint8_t*>(img), u, y, k, c.nc, c.ntiles, lmax, cols,
+                                           c.d_status);
   TETMF_LAUNCH_CK();
   return FEM_OK;
 }
 
-template <int ND, int NQ, bool BF16>
+template <int ND, int NQ, bool BF16, bool X3>
 int launch(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) {
   if (int e = init_rows<float>(y, u, c.d_mask, c.ndofs, 0.0f, st)) return e;
-  return k ? launch_g<ND, NQ, BF16, true>(c, u, y, k, st) : launch_g<ND, NQ, BF16, false>(c, u, y, k, st);
+  return k ? launch_g<ND, NQ, BF16, true, X3>(c, u, y, k, st) : launch_g<ND, NQ, BF16, false, X3>(c, u, y, k, st);
+}
+
+template <int ND, int NQ>
+int launch_prec(Ctx& c, int prec, const float* u, float* y, const float* k, cudaStream_t st) {
+  if (prec == FEM_BF16) return launch<ND, NQ, true, false>(c, u, y, k, st);
+  if (prec == FEM_TF32X3) {
+    if constexpr (ND > 20) {
+      // p = 4: the high and low images of both tables (155 KB) leave no room for the tile stages
+      set_error("FEM_TF32X3 is offered for degrees 1 to 3");
+      return FEM_EUNSUPPORTED;
+    } else {
+      return launch<ND, NQ, false, true>(c, u, y, k, st);
+    }
+  }
+  return launch<ND, NQ, false, false>(c, u, y, k, st);
 }
 
 }  // namespace
@@ -450,12 +518,11 @@ int cg_apply_tc(Ctx& c, int prec, const void* u, void* y, const void* k, void* s
   const float* uf = static_cast<const float*>(u);
   float* yf = static_cast<float*>(y);
   const float* kf = static_cast<const float*>(k);
-  const bool bf = prec == FEM_BF16;
   switch (c.p) {
-    case 1: return bf ? launch<4, 5, true>(c, uf, yf, kf, st) : launch<4, 5, false>(c, uf, yf, kf, st);
-    case 2: return bf ? launch<10, 15, true>(c, uf, yf, kf, st) : launch<10, 15, false>(c, uf, yf, kf, st);
-    case 3: return bf ? launch<20, 35, true>(c, uf, yf, kf, st) : launch<20, 35, false>(c, uf, yf, kf, st);
-    case 4: return bf ? launch<35, 70, true>(c, uf, yf, kf, st) : launch<35, 70, false>(c, uf, yf, kf, st);
+    case 1: return launch_prec<4, 5>(c, prec, uf, yf, kf, st);
+    case 2: return launch_prec<10, 15>(c, prec, uf, yf, kf, st);
+    case 3: return launch_prec<20, 35>(c, prec, uf, yf, kf, st);
+    case 4: return launch_prec<35, 70>(c, prec, uf, yf, kf, st);
   }
   set_error("degree %d not supported", c.p);
   return FEM_EUNSUPPORTED;

@@ -78,6 +78,7 @@ struct Ctx {
   // tensor-core operand images (shared-memory byte images of E^T and E)
   void* d_tc_tf32 = nullptr;
   void* d_tc_bf16 = nullptr;
+  void* d_tc_tf32x3 = nullptr;      // high then low TF32 parts (3xTF32)
   // DG tensor-core face loop: interior faces in tiles of 128 faces sharing (f-, f+, orientation)
   int64_t dg_ntiles = 0;
   int32_t* d_dgt_code = nullptr;    // [dg_ntiles] (f- * 4 + f+) * 6 + o

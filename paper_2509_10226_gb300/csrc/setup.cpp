@@ -638,6 +638,7 @@ int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k,
   if (c.kind == FEM_DG) {
     if (k) return set_error("fem_apply: DG supports k = NULL only"), FEM_EUNSUPPORTED;
     if (prec == FEM_TF32 || prec == FEM_BF16) return dg_apply_tc(c, prec, u, y, stream);
+    if (prec == FEM_TF32X3) return set_error("fem_apply: FEM_TF32X3 is offered for CG only"), FEM_EUNSUPPORTED;
     if (prec != FEM_FP64 && prec != FEM_FP32)
       return set_error("fem_apply: unknown precision %d", prec), FEM_EUNSUPPORTED;
     return dg_apply(c, prec, u, y, stream);
@@ -648,6 +649,7 @@ int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k,
       return cg_apply_simt(c, prec, u, y, k, false, stream);
     case FEM_TF32:
     case FEM_BF16:
+    case FEM_TF32X3:
       return cg_apply_tc(c, prec, u, y, k, stream);
     default:
       return set_error("fem_apply: unknown precision %d", prec), FEM_EUNSUPPORTED;
@@ -723,8 +725,8 @@ int fem_solve(fem_ctx* ctx, const fem_solve_opts* opts, const double* b, double*
   if (opts->mode != FEM_SOLVE_FP64_PCG && opts->mode != FEM_SOLVE_IR_MIXED)
     return set_error("fem_solve: bad mode"), FEM_EINVAL;
   if (opts->mode == FEM_SOLVE_IR_MIXED && opts->inner_prec != FEM_FP32 && opts->inner_prec != FEM_TF32 &&
-      opts->inner_prec != FEM_BF16)
-    return set_error("fem_solve: inner_prec must be FEM_FP32, FEM_TF32 or FEM_BF16"), FEM_EUNSUPPORTED;
+      opts->inner_prec != FEM_BF16 && opts->inner_prec != FEM_TF32X3)
+    return set_error("fem_solve: inner_prec must be FEM_FP32, FEM_TF32, FEM_BF16 or FEM_TF32X3"), FEM_EUNSUPPORTED;
   if (!(opts->rtol > 0) || opts->max_inner < 1 || opts->max_outer < 1)
     return set_error("fem_solve: need rtol > 0, max_inner >= 1, max_outer >= 1"), FEM_EINVAL;
   return solve(ctx->c, opts, b, x, stats, stream);

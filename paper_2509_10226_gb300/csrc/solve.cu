@@ -463,8 +463,8 @@ extern "C" int fem_solve_noalloc(fem_ctx* ctx, const fem_solve_opts* opts, const
     return FEM_EINVAL;
   }
   if (opts->mode == FEM_SOLVE_IR_MIXED && opts->inner_prec != FEM_FP32 && opts->inner_prec != FEM_TF32 &&
-      opts->inner_prec != FEM_BF16) {
-    set_error("fem_solve_noalloc: inner_prec must be FEM_FP32, FEM_TF32 or FEM_BF16");
+      opts->inner_prec != FEM_BF16 && opts->inner_prec != FEM_TF32X3) {
+    set_error("fem_solve_noalloc: inner_prec must be FEM_FP32, FEM_TF32, FEM_BF16 or FEM_TF32X3");
     return FEM_EUNSUPPORTED;
   }
   if (!(opts->rtol > 0) || opts->max_inner < 1 || opts->max_outer < 1) {

@@ -99,6 +99,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
+// TF32 high part of an FP32 value (the 19 bits the tensor core reads); value - high part is
+// exact in FP32 and is the low part of a 3xTF32 split
+__device__ __forceinline__ uint32_t tf32_hi(uint32_t bits) { return bits & 0xFFFFE000u; }
+
 // write one K-major row (row m) of K values into a 128-row operand (LBO = 16 * 128)
 template <int K, bool BF16>
 __device__ __forceinline__ void write_row(uint8_t* base, int m, const float* v) {
@@ -203,10 +207,11 @@ __device__ __forceinline__ uint64_t splat2(float v) {
 // points (8 pairs, 48 columns); columns past the last pair in the last chunk are zeroed.
 // TF32: FP32 bits, one column per element; BF16: pairs packed into one column (Q column e / 2),
 // which never overtakes the columns still to be read.  kq = this cell's coefficients at the NQ
-// points, or null.
-template <int ND, int NQ, bool BF16, bool HAS_K>
+// points, or null.  X3 (3xTF32): Q is split into a TF32 high part (kept in place) and the
+// remainder (exact in FP32, stored at column offset qlo), for the three-product GEMM 2.
+template <int ND, int NQ, bool BF16, bool HAS_K, bool X3 = false>
 __device__ __forceinline__ void metric_to_q(uint32_t lane_base, float m0, float m1, float m2, float m3, float m4,
-                                            float m5, const float* kq) {
+                                            float m5, const float* kq, uint32_t qlo = 0) {
   constexpr int NP = (NQ + 1) / 2;  // point pairs
   constexpr int NCHUNK = (NP + 7) / 8;
   const uint64_t M0 = splat2(m0), M1 = splat2(m1), M2 = splat2(m2), M3 = splat2(m3), M4 = splat2(m4),
@@ -252,7 +257,19 @@ __device__ __forceinline__ void metric_to_q(uint32_t lane_base, float m0, float 
     } else {
 #pragma unroll
       for (int l = 0; l < 3; ++l)
-        if (l < nl) tmem_st16(lane_base + 48 * c + 16 * l, d + 16 * l);
+        if (l < nl) {
+          if constexpr (X3) {
+            uint32_t lo[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const uint32_t h = tf32_hi(d[16 * l + i]);
+              lo[i] = __float_as_uint(__uint_as_float(d[16 * l + i]) - __uint_as_float(h));
+              d[16 * l + i] = h;
+            }
+            tmem_st16(lane_base + qlo + 48 * c + 16 * l, lo);
+          }
+          tmem_st16(lane_base + 48 * c + 16 * l, d + 16 * l);
+        }
     }
   }
 }

@@ -13,7 +13,8 @@ import torch
 from . import _lib
 from ._lib import call
 
-PREC = {"fp64": _lib.FEM_FP64, "fp32": _lib.FEM_FP32, "tf32": _lib.FEM_TF32, "bf16": _lib.FEM_BF16}
+PREC = {"fp64": _lib.FEM_FP64, "fp32": _lib.FEM_FP32, "tf32": _lib.FEM_TF32, "bf16": _lib.FEM_BF16,
+        "tf32x3": _lib.FEM_TF32X3}
 
 
 def _vec_dtype(prec: str):

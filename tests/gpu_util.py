@@ -14,7 +14,11 @@ torch = pytest.importorskip("torch")
 #         FP32 metric give a few units of that, cancellation in y = A u (rows sum
 #         to zero) amplifies it by the ratio of term size to result size (~3-5)
 #   bf16: 4e-2  BF16 keeps 7 mantissa bits: unit roundoff 2^-8 = 3.9e-3, same chain
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32": 5e-3, "bf16": 4e-2}
+#   tf32x3: 1e-5  each operand is split into a TF32 high part and a TF32 low part and three
+#         products (hi hi + hi lo + lo hi) are accumulated in FP32: the dropped lo*lo term and
+#         the truncation of the low parts are below 2^-20 relative, so the result is as accurate
+#         as the FP32 path (same bound)
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32": 5e-3, "bf16": 4e-2, "tf32x3": 1e-5}
 
 
 def require_gpu():

@@ -131,7 +131,7 @@ def test_autograd_function():
     assert abs(fd - kd.grad[e].item()) < 1e-8 * max(1.0, abs(fd))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16", "tf32x3"])
 def test_config2_full_size_sampled(prec):
     """CG P3 on the 64^3 Kuhn cube (1,572,864 cells, 7,189,057 DoFs), Morton order, the launch the
     benchmark times: 512 sampled rows against the oracle, plus A 1 = 0 and u^T A u = |a|^2."""
@@ -160,19 +160,25 @@ def test_config2_full_size_sampled(prec):
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
-@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "tf32x3"])
 def test_tensor_core_degrees_ragged(p, prec):
     """tcgen05 path, p = 1..4, 3^3 cube (one full tile + a 34-cell tail), shuffled input order."""
     sp, xyz, cells, dofs, keys = make(3, p, shuffle=True, seed=p)
     perm = sp.dof_permutation()
     u = synth.uniform_vector(sp.n_dofs, 1)
+    if prec == "tf32x3" and p == 4:
+        from paper_2509_10226_gb300 import FemError
+
+        with pytest.raises(FemError, match="degrees 1 to 3"):
+            sp.apply(to_dev(u[perm], prec), prec=prec)
+        return
     y_ref = cg.apply(xyz, cells, u, p, dofs=dofs)
     y = to_host(sp.apply(to_dev(u[perm], prec), prec=prec))
     assert_close(y, y_ref[perm], prec, f"p={p}")
     assert sp.device_status() == 0
 
 
-@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "tf32x3"])
 def test_tensor_core_config1_variable_k_dirichlet(prec):
     """Config-1 mesh (8^3, 24 tiles) on the tensor cores: plain, with k ~ lognormal(0, 0.5), and with
     Dirichlet rows; several tiles per persistent CTA are exercised on the 64^3 test below."""

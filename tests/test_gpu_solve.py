@@ -32,7 +32,8 @@ def oracle_residual(xyz, cells, p, dofs, mask, x_can, b_can):
     return np.linalg.norm(r) / np.linalg.norm(b_can)
 
 
-@pytest.mark.parametrize("mode,inner", [("pcg", "fp32"), ("ir", "fp32"), ("ir", "tf32"), ("ir", "bf16")])
+@pytest.mark.parametrize("mode,inner",
+                         [("pcg", "fp32"), ("ir", "fp32"), ("ir", "tf32"), ("ir", "bf16"), ("ir", "tf32x3")])
 def test_solve_p3_small(mode, inner):
     p = 3
     sp, xyz, cells, dofs, keys, mask = setup_problem(6, p)
