@@ -30,9 +30,10 @@ def geometry(xyz: np.ndarray, cells: np.ndarray):
     return J, det, Jinv
 
 
-def tables(p: int):
-    """(x_hat [nq,3], w [nq], E as grad table [nq, ndof, 3], values [nq, ndof])."""
-    xq, wq = quadrature.tet_rule(p)
+def tables(p: int, modified: bool = False):
+    """(x_hat [nq,3], w [nq], E as grad table [nq, ndof, 3], values [nq, ndof]); modified selects the
+    cell rule of Sec. 3.3."""
+    xq, wq = quadrature.tet_rule(p, modified)
     return xq, wq, basis.gradients(p, xq), basis.values(p, xq)
 
 
@@ -52,9 +53,9 @@ def _qp_operator(Jinv, det, wq, k, transpose=False):
     return D
 
 
-def element_apply(xyz, cells, ue, p, k=None, transpose=False):
+def element_apply(xyz, cells, ue, p, k=None, transpose=False, modified=False):
     """Local products y_e = E^T D_e E u_e for every cell; ue [C, ndof] -> [C, ndof]."""
-    xq, wq, G, _ = tables(p)
+    xq, wq, G, _ = tables(p, modified)
     C = ue.shape[0]
     out = np.empty_like(ue, dtype=np.float64)
     for s in range(0, C, CHUNK):
@@ -82,7 +83,7 @@ def _scatter(dofs, ye, n):
     return y
 
 
-def apply(xyz, cells, u, p, k=None, dirichlet_mask=None, dofs=None):
+def apply(xyz, cells, u, p, k=None, dirichlet_mask=None, dofs=None, modified=False):
     """y = A(k) u in canonical numbering.
 
     With a Dirichlet mask P (True = constrained) the operator is P A P + (I - P):
@@ -92,25 +93,25 @@ def apply(xyz, cells, u, p, k=None, dirichlet_mask=None, dofs=None):
         dofs, _ = topology.cg_numbering(cells, p)
     u = np.asarray(u, dtype=np.float64)
     uu = u if dirichlet_mask is None else np.where(dirichlet_mask, 0.0, u)
-    y = _scatter(dofs, element_apply(xyz, cells, uu[dofs], p, k), u.shape[0])
+    y = _scatter(dofs, element_apply(xyz, cells, uu[dofs], p, k, modified=modified), u.shape[0])
     if dirichlet_mask is not None:
         y = np.where(dirichlet_mask, u, y)
     return y
 
 
-def apply_adjoint(xyz, cells, g, p, k=None, dirichlet_mask=None, dofs=None):
+def apply_adjoint(xyz, cells, g, p, k=None, dirichlet_mask=None, dofs=None, modified=False):
     """A(k)^T g: the transposed chain G_e^T E^T D_e^T E G_e summed over cells."""
     if dofs is None:
         dofs, _ = topology.cg_numbering(cells, p)
     g = np.asarray(g, dtype=np.float64)
     gg = g if dirichlet_mask is None else np.where(dirichlet_mask, 0.0, g)
-    out = _scatter(dofs, element_apply(xyz, cells, gg[dofs], p, k, transpose=True), g.shape[0])
+    out = _scatter(dofs, element_apply(xyz, cells, gg[dofs], p, k, transpose=True, modified=modified), g.shape[0])
     if dirichlet_mask is not None:
         out = np.where(dirichlet_mask, g, out)
     return out
 
 
-def coeff_grad(xyz, cells, u, g, p, k=None, dofs=None):
+def coeff_grad(xyz, cells, u, g, p, k=None, dofs=None, modified=False):
     """Backward of L = <g, A(k) u>: (dL/du = A(k)^T g, dL/dk [C, nq]).
 
     dL/dk_{e,q} = w_q |det J_e| (grad u(x_q) . grad g(x_q)) with physical
@@ -118,7 +119,7 @@ def coeff_grad(xyz, cells, u, g, p, k=None, dofs=None):
     """
     if dofs is None:
         dofs, _ = topology.cg_numbering(cells, p)
-    xq, wq, G, _ = tables(p)
+    xq, wq, G, _ = tables(p, modified)
     C = cells.shape[0]
     dk = np.empty((C, wq.shape[0]))
     for s in range(0, C, CHUNK):
@@ -127,14 +128,14 @@ def coeff_grad(xyz, cells, u, g, p, k=None, dofs=None):
         gu = np.einsum("cak,cqa->cqk", Jinv, np.einsum("qjk,cj->cqk", G, u[dofs[e]]))
         gg = np.einsum("cak,cqa->cqk", Jinv, np.einsum("qjk,cj->cqk", G, g[dofs[e]]))
         dk[e] = wq[None, :] * np.abs(det)[:, None] * np.einsum("cqk,cqk->cq", gu, gg)
-    return apply_adjoint(xyz, cells, g, p, k, dofs=dofs), dk
+    return apply_adjoint(xyz, cells, g, p, k, dofs=dofs, modified=modified), dk
 
 
-def diagonal(xyz, cells, p, n, k=None, dirichlet_mask=None, dofs=None):
+def diagonal(xyz, cells, p, n, k=None, dirichlet_mask=None, dofs=None, modified=False):
     """diag(A): sum over cells and quadrature points of (J^-T grad phi_i)^T k w |detJ| (J^-T grad phi_i)."""
     if dofs is None:
         dofs, _ = topology.cg_numbering(cells, p)
-    xq, wq, G, _ = tables(p)
+    xq, wq, G, _ = tables(p, modified)
     C = cells.shape[0]
     de = np.empty((C, G.shape[1]))
     for s in range(0, C, CHUNK):
@@ -151,11 +152,11 @@ def diagonal(xyz, cells, p, n, k=None, dirichlet_mask=None, dofs=None):
     return d
 
 
-def rhs_const(xyz, cells, p, n, f=1.0, dirichlet_mask=None, dofs=None):
+def rhs_const(xyz, cells, p, n, f=1.0, dirichlet_mask=None, dofs=None, modified=False):
     """b_i = sum_e sum_q w_q |det J| phi_i(x_q) f for a constant source f (Sec. 2.1 weak form)."""
     if dofs is None:
         dofs, _ = topology.cg_numbering(cells, p)
-    xq, wq, _, V = tables(p)
+    xq, wq, _, V = tables(p, modified)
     _, det, _ = geometry(xyz, cells)
     be = f * np.abs(det)[:, None] * (wq @ V)[None, :]
     b = _scatter(dofs, be, n)

@@ -60,15 +60,16 @@ def _face_geometry(xyz, cells, c, m, p):
     return pts, wq2[None, :] * two_area[:, None], n, 0.5 * two_area
 
 
-def apply(xyz, cells, u, p, penalty_factor=None, include_boundary=True):
-    """y = A_DG u with u in canonical DG numbering (cell-major, e * ndof + j)."""
+def apply(xyz, cells, u, p, penalty_factor=None, include_boundary=True, modified=False):
+    """y = A_DG u with u in canonical DG numbering (cell-major, e * ndof + j).  modified selects the
+    cell rule of Sec. 3.3 for the cell term; face integrals keep the standard rule."""
     xyz = np.asarray(xyz, dtype=np.float64)
     cells = np.asarray(cells, dtype=np.int64)
     eta = default_penalty(p) if penalty_factor is None else float(penalty_factor)
     nd = basis.num_dofs(p)
     C = cells.shape[0]
     ue = np.asarray(u, dtype=np.float64).reshape(C, nd)
-    y = element_apply(xyz, cells, ue, p)  # cell term, Eq. 3 on discontinuous DoFs
+    y = element_apply(xyz, cells, ue, p, modified=modified)  # cell term, Eq. 3 on discontinuous DoFs
     interior, boundary = topology.faces(cells)
 
     for s in range(0, interior.shape[0], CHUNK):

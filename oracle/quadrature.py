@@ -57,9 +57,10 @@ def gm_rule(s: int, n: int):
     return lam[:, 1:].copy(), np.array([float(w) for w in wts], dtype=np.float64)
 
 
-def tet_rule(p: int):
-    """Cell rule for degree p: GM with s = p (exact to degree 2p+1)."""
-    return gm_rule(p, 3)
+def tet_rule(p: int, modified: bool = False):
+    """Cell rule for degree p: GM with s = p (exact to degree 2p+1); with modified=True the rule of
+    Sec. 3.3, exact to degree 2p-2, taken as GM with s = p-1 (exact to degree 2p-1)."""
+    return gm_rule(p - 1 if modified else p, 3)
 
 
 def tri_rule(p: int):

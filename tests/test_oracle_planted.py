@@ -56,8 +56,8 @@ def test_signed_determinant_is_caught(monkeypatch):
 def test_dropped_quadrature_point_is_caught(monkeypatch):
     orig = quadrature.tet_rule
 
-    def wrong(p):
-        x, w = orig(p)
+    def wrong(p, modified=False):
+        x, w = orig(p, modified)
         return x[:-1], w[:-1]
 
     monkeypatch.setattr(quadrature, "tet_rule", wrong)
@@ -118,3 +118,14 @@ def test_dg_normal_sign_is_caught(monkeypatch):
     monkeypatch.setattr(dg, "_face_geometry", wrong)
     with pytest.raises(AssertionError):
         test_linear_field_with_boundary_terms()
+
+
+def test_too_small_modified_rule_is_caught(monkeypatch):
+    """A modified rule one order too small (s = p - 2, exact to 2p - 3) fails the brute-force pin."""
+    from tests.test_oracle_modified_rule import test_modified_element_matrix_brute_force
+
+    test_modified_element_matrix_brute_force(3)
+    orig = quadrature.tet_rule
+    monkeypatch.setattr(quadrature, "tet_rule", lambda p, modified=False: orig(p - 1 if modified else p, modified))
+    with pytest.raises(AssertionError):
+        test_modified_element_matrix_brute_force(3)
