@@ -18,8 +18,9 @@
  *
  * Conventions fixed by this library (the paper leaves them open):
  *   - quadrature: Grundmann-Moeller with s = p on cells (nq = 5/15/35/70 for
- *     p = 1..4) and on faces (nqf = 4/10/20/35); point order i ascending then
- *     beta lexicographic ascending; coefficient arrays k/dk use this order;
+ *     p = 1..4; s = p - 1 with FEM_RULE_MODIFIED) and on faces (nqf =
+ *     4/10/20/35); point order i ascending then beta lexicographic ascending;
+ *     coefficient arrays k/dk use this order;
  *   - J = [x1-x0 | x2-x0 | x3-x0] from the user's vertex order of each cell;
  *     |det J| is used, so either orientation is accepted;
  *   - local shape-function order: beta in N^4, |beta| = p, lexicographic
@@ -81,6 +82,12 @@ extern "C" {
 #define FEM_REORDER_NONE 0
 #define FEM_REORDER_MORTON 1
 
+/* cell quadrature (face integrals always use the standard rule) */
+#define FEM_RULE_STANDARD 0  /* Grundmann-Moeller s = p: exact to degree 2p+1      */
+#define FEM_RULE_MODIFIED 1  /* s = p-1: exact to degree 2p-1 >= 2p-2, the degree */
+                             /* of grad phi_i . grad phi_j on an affine cell      */
+                             /* (Sec. 3.3); nq = 1/5/15/35 for p = 1..4          */
+
 #define FEM_SOLVE_FP64_PCG 0   /* Jacobi-PCG, FP64 operator and vectors      */
 #define FEM_SOLVE_IR_MIXED 1   /* FP64 iterative refinement around an inner  */
                                /* FP32-vector Jacobi-PCG (inner_prec apply)  */
@@ -104,6 +111,7 @@ typedef struct {
   double dg_penalty_factor;  /* eta; <= 0 selects (p+1)(p+3)                 */
   int32_t device;            /* CUDA device ordinal; -1 builds a host-only   */
                              /* plan: queries work, hot calls return EINVAL  */
+  int32_t cell_rule;         /* FEM_RULE_STANDARD (0) or FEM_RULE_MODIFIED   */
 } fem_space_desc;
 
 /* ---- set-up (synchronous) ------------------------------------------ */

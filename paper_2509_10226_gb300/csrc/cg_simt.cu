@@ -291,24 +291,15 @@ int launch_rhs(Ctx& c, double f, double* b, cudaStream_t st) {
   return FEM_OK;
 }
 
-#define TETMF_DISPATCH_P(p, CALL)                                        \
-  switch (p) {                                                          \
-    case 1: { constexpr int ND = 4, NQ = 5; return CALL; }              \
-    case 2: { constexpr int ND = 10, NQ = 15; return CALL; }            \
-    case 3: { constexpr int ND = 20, NQ = 35; return CALL; }            \
-    case 4: { constexpr int ND = 35, NQ = 70; return CALL; }            \
-    default: set_error("degree %d not supported", p); return FEM_EUNSUPPORTED; \
-  }
-
 }  // namespace
 
 int cg_apply_simt(Ctx& c, int prec, const void* u, void* y, const void* k, bool /*transpose*/, void* stream) {
   cudaStream_t st = as_stream(stream);
   if (prec == FEM_FP64) {
-    TETMF_DISPATCH_P(c.p, (launch_apply<ND, NQ, double>(c, static_cast<const double*>(u), static_cast<double*>(y),
+    TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_apply<ND, NQ, double>(c, static_cast<const double*>(u), static_cast<double*>(y),
                                                         static_cast<const double*>(k), c.d_metric64, c.d_tab64, st)))
   }
-  TETMF_DISPATCH_P(c.p, (launch_apply<ND, NQ, float>(c, static_cast<const float*>(u), static_cast<float*>(y),
+  TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_apply<ND, NQ, float>(c, static_cast<const float*>(u), static_cast<float*>(y),
                                                      static_cast<const float*>(k), c.d_metric32, c.d_tab32, st)))
 }
 
@@ -316,12 +307,12 @@ int cg_coeff_grad(Ctx& c, int prec, const void* u, const void* g, const void* k,
                   void* stream) {
   cudaStream_t st = as_stream(stream);
   if (prec == FEM_FP64) {
-    TETMF_DISPATCH_P(c.p, (launch_coeff_grad<ND, NQ, double>(
+    TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_coeff_grad<ND, NQ, double>(
                               c, static_cast<const double*>(u), static_cast<const double*>(g),
                               static_cast<const double*>(k), static_cast<double*>(grad_u), static_cast<double*>(dk),
                               c.d_metric64, c.d_tab64, st)))
   }
-  TETMF_DISPATCH_P(c.p, (launch_coeff_grad<ND, NQ, float>(
+  TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_coeff_grad<ND, NQ, float>(
                             c, static_cast<const float*>(u), static_cast<const float*>(g),
                             static_cast<const float*>(k), static_cast<float*>(grad_u), static_cast<float*>(dk),
                             c.d_metric32, c.d_tab32, st)))
@@ -330,16 +321,16 @@ int cg_coeff_grad(Ctx& c, int prec, const void* u, const void* g, const void* k,
 int cg_diagonal(Ctx& c, int prec, void* d, const void* k, void* stream) {
   cudaStream_t st = as_stream(stream);
   if (prec == FEM_FP64) {
-    TETMF_DISPATCH_P(c.p, (launch_diag<ND, NQ, double>(c, static_cast<double*>(d), static_cast<const double*>(k),
+    TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_diag<ND, NQ, double>(c, static_cast<double*>(d), static_cast<const double*>(k),
                                                        c.d_metric64, c.d_tab64, st)))
   }
-  TETMF_DISPATCH_P(c.p, (launch_diag<ND, NQ, float>(c, static_cast<float*>(d), static_cast<const float*>(k),
+  TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_diag<ND, NQ, float>(c, static_cast<float*>(d), static_cast<const float*>(k),
                                                     c.d_metric32, c.d_tab32, st)))
 }
 
 int cg_rhs_const(Ctx& c, double f, double* b, void* stream) {
   cudaStream_t st = as_stream(stream);
-  TETMF_DISPATCH_P(c.p, (launch_rhs<ND, NQ>(c, f, b, st)))
+  TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_rhs<ND, NQ>(c, f, b, st)))
 }
 
 }  // namespace tetmf

@@ -503,29 +503,14 @@ int launch_prec(Ctx& c, int prec, const float* u, float* y, const float* k, cuda
 
 }  // namespace
 
-int tc_prepare(Ctx& c) {
-  switch (c.p) {
-    case 1: return prepare<4, 5>(c);
-    case 2: return prepare<10, 15>(c);
-    case 3: return prepare<20, 35>(c);
-    case 4: return prepare<35, 70>(c);
-  }
-  return FEM_OK;
-}
+int tc_prepare(Ctx& c) { TETMF_DISPATCH_SPACE(c.p, c.nq, (prepare<ND, NQ>(c))) }
 
 int cg_apply_tc(Ctx& c, int prec, const void* u, void* y, const void* k, void* stream) {
   cudaStream_t st = as_stream(stream);
   const float* uf = static_cast<const float*>(u);
   float* yf = static_cast<float*>(y);
   const float* kf = static_cast<const float*>(k);
-  switch (c.p) {
-    case 1: return launch_prec<4, 5>(c, prec, uf, yf, kf, st);
-    case 2: return launch_prec<10, 15>(c, prec, uf, yf, kf, st);
-    case 3: return launch_prec<20, 35>(c, prec, uf, yf, kf, st);
-    case 4: return launch_prec<35, 70>(c, prec, uf, yf, kf, st);
-  }
-  set_error("degree %d not supported", c.p);
-  return FEM_EUNSUPPORTED;
+  TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_prec<ND, NQ>(c, prec, uf, yf, kf, st)))
 }
 
 }  // namespace tetmf

@@ -68,3 +68,21 @@ inline int init_rows(T* y, const T* u, const uint8_t* mask, int64_t n, T fixed, 
 }
 
 }  // namespace tetmf
+
+// Compile-time shapes of the supported spaces: degree p (ND = (p+1)(p+2)(p+3)/6 DoFs per cell)
+// with the standard cell rule (Grundmann-Moeller s = p, NQ points) or the modified one of Sec. 3.3
+// (s = p - 1); NQF = face points (always s = p).  CALL may use ND, NQ and NQF.
+#define TETMF_DISPATCH_SPACE(p, nq, CALL)                                                        \
+  switch ((p) * 100 + (nq)) {                                                                   \
+    case 105: { constexpr int ND = 4, NQ = 5, NQF = 4; (void)NQF; return CALL; }                \
+    case 101: { constexpr int ND = 4, NQ = 1, NQF = 4; (void)NQF; return CALL; }                \
+    case 215: { constexpr int ND = 10, NQ = 15, NQF = 10; (void)NQF; return CALL; }             \
+    case 205: { constexpr int ND = 10, NQ = 5, NQF = 10; (void)NQF; return CALL; }              \
+    case 335: { constexpr int ND = 20, NQ = 35, NQF = 20; (void)NQF; return CALL; }             \
+    case 315: { constexpr int ND = 20, NQ = 15, NQF = 20; (void)NQF; return CALL; }             \
+    case 470: { constexpr int ND = 35, NQ = 70, NQF = 35; (void)NQF; return CALL; }             \
+    case 435: { constexpr int ND = 35, NQ = 35, NQF = 35; (void)NQF; return CALL; }             \
+    default:                                                                                    \
+      ::tetmf::set_error("degree %d with %d cell quadrature points not supported", int(p), int(nq)); \
+      return FEM_EUNSUPPORTED;                                                                  \
+  }

@@ -246,30 +246,21 @@ int launch_boundary32(Ctx& c, const float* u, float* y, cudaStream_t st) {
   return FEM_OK;
 }
 
-#define TETMF_DISPATCH_DG(p, CALL)                                                \
-  switch (p) {                                                                   \
-    case 1: { constexpr int ND = 4, NQ = 5, NQF = 4; return CALL; }               \
-    case 2: { constexpr int ND = 10, NQ = 15, NQF = 10; return CALL; }            \
-    case 3: { constexpr int ND = 20, NQ = 35, NQF = 20; return CALL; }            \
-    case 4: { constexpr int ND = 35, NQ = 70, NQF = 35; return CALL; }            \
-    default: set_error("degree %d not supported", p); return FEM_EUNSUPPORTED;    \
-  }
-
 }  // namespace
 
 int dg_apply(Ctx& c, int prec, const void* u, void* y, void* stream) {
   cudaStream_t st = as_stream(stream);
   if (prec == FEM_FP64) {
-    TETMF_DISPATCH_DG(c.p, (launch_dg<ND, NQ, NQF, double>(c, static_cast<const double*>(u), static_cast<double*>(y),
+    TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_dg<ND, NQ, NQF, double>(c, static_cast<const double*>(u), static_cast<double*>(y),
                                                            c.d_metric64, c.d_tab64, c.d_fi_geo64, c.d_fb_geo64, st)))
   }
-  TETMF_DISPATCH_DG(c.p, (launch_dg<ND, NQ, NQF, float>(c, static_cast<const float*>(u), static_cast<float*>(y),
+  TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_dg<ND, NQ, NQF, float>(c, static_cast<const float*>(u), static_cast<float*>(y),
                                                         c.d_metric32, c.d_tab32, c.d_fi_geo32, c.d_fb_geo32, st)))
 }
 
 int dg_boundary_fp32(Ctx& c, const float* u, float* y, void* stream) {
   cudaStream_t st = as_stream(stream);
-  TETMF_DISPATCH_DG(c.p, (launch_boundary32<ND, NQF>(c, u, y, st)))
+  TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_boundary32<ND, NQF>(c, u, y, st)))
 }
 
 }  // namespace tetmf

@@ -718,14 +718,8 @@ int dg_apply_tc(Ctx& c, int prec, const void* u, void* y, void* stream) {
   const float* uf = static_cast<const float*>(u);
   float* yf = static_cast<float*>(y);
   const bool bf = prec == FEM_BF16;
-  switch (c.p) {
-    case 1: return bf ? launch_dg_tc<4, 5, 4, true>(c, uf, yf, st) : launch_dg_tc<4, 5, 4, false>(c, uf, yf, st);
-    case 2: return bf ? launch_dg_tc<10, 15, 10, true>(c, uf, yf, st) : launch_dg_tc<10, 15, 10, false>(c, uf, yf, st);
-    case 3: return bf ? launch_dg_tc<20, 35, 20, true>(c, uf, yf, st) : launch_dg_tc<20, 35, 20, false>(c, uf, yf, st);
-    case 4: return bf ? launch_dg_tc<35, 70, 35, true>(c, uf, yf, st) : launch_dg_tc<35, 70, 35, false>(c, uf, yf, st);
-  }
-  set_error("degree %d not supported", c.p);
-  return FEM_EUNSUPPORTED;
+  if (bf) TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_dg_tc<ND, NQ, NQF, true>(c, uf, yf, st)))
+  TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_dg_tc<ND, NQ, NQF, false>(c, uf, yf, st)))
 }
 
 }  // namespace tetmf

@@ -26,7 +26,9 @@ struct RefTables {
   std::vector<int32_t> fperm; // [6][nqf] face point index seen from the other side
 };
 
-void build_tables(int p, RefTables& t);
+// cell rule: Grundmann-Moeller with s = s_cell (p, or p - 1 for the modified integration of
+// Sec. 3.3); face rule: s = p
+void build_tables(int p, int s_cell, RefTables& t);
 
 struct Ctx {
   // plan

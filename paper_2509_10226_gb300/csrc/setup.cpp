@@ -482,6 +482,10 @@ int fem_create(const fem_mesh_desc* mesh, const fem_space_desc* space, fem_ctx**
     set_error("fem_create: dirichlet must be 0 or 1");
     return FEM_EINVAL;
   }
+  if (space->cell_rule != FEM_RULE_STANDARD && space->cell_rule != FEM_RULE_MODIFIED) {
+    set_error("fem_create: cell_rule must be FEM_RULE_STANDARD or FEM_RULE_MODIFIED");
+    return FEM_EINVAL;
+  }
   if (space->dirichlet && space->kind == FEM_DG) {
     set_error("fem_create: the DG space imposes Dirichlet data weakly; dirichlet must be 0");
     return FEM_EINVAL;
@@ -502,7 +506,7 @@ int fem_create(const fem_mesh_desc* mesh, const fem_space_desc* space, fem_ctx**
   c.nc = mesh->n_cells;
   int st = FEM_OK;
   try {
-    build_tables(c.p, c.tab);
+    build_tables(c.p, space->cell_rule == FEM_RULE_MODIFIED ? c.p - 1 : c.p, c.tab);
     c.nd = c.tab.nd;
     c.nq = c.tab.nq;
     c.nqf = c.tab.nqf;

@@ -111,13 +111,13 @@ void eval_basis(int p, const std::vector<std::vector<int>>& nodes, const double 
 
 }  // namespace
 
-void build_tables(int p, RefTables& t) {
+void build_tables(int p, int s_cell, RefTables& t) {
   t.p = p;
   const auto nodes = compositions(p, 4);
   t.nd = int(nodes.size());
   const int nd = t.nd;
 
-  const SimplexRule cell = gm_rule(p, 3);
+  const SimplexRule cell = gm_rule(s_cell, 3);
   t.nq = int(cell.w.size());
   t.xq.assign(size_t(t.nq) * 3, 0.0);
   t.wq = cell.w;

@@ -34,16 +34,19 @@ class FemSpace:
     """A mesh + finite-element space + device plan (one fem_ctx).
 
     xyz [nv, 3] float64 and cells [nc, 4] int32 are host arrays in the user's
-    numbering.  device = -1 builds a host-only plan (queries only).
+    numbering.  device = -1 builds a host-only plan (queries only).  modified_rule selects the
+    cell rule exact to degree 2p - 2 (Sec. 3.3; faces keep the standard rule).
     """
 
-    def __init__(self, xyz, cells, kind="cg", degree=1, dirichlet=False, reorder=True, penalty=None, device=0):
+    def __init__(self, xyz, cells, kind="cg", degree=1, dirichlet=False, reorder=True, penalty=None, device=0,
+                 modified_rule=False):
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int32)
         mesh = _lib.MeshDesc(xyz.shape[0], xyz.ctypes.data, cells.shape[0], cells.ctypes.data)
         space = _lib.SpaceDesc(_lib.FEM_CG if kind == "cg" else _lib.FEM_DG, int(degree), int(bool(dirichlet)),
                                _lib.FEM_REORDER_MORTON if reorder else _lib.FEM_REORDER_NONE,
-                               float(penalty) if penalty else 0.0, int(device))
+                               float(penalty) if penalty else 0.0, int(device),
+                               _lib.FEM_RULE_MODIFIED if modified_rule else _lib.FEM_RULE_STANDARD)
         h = ctypes.c_void_p()
         call("fem_create", ctypes.byref(mesh), ctypes.byref(space), ctypes.byref(h))
         self._h = h
