@@ -277,6 +277,7 @@ def main():
     ap.add_argument("--no-dg", action="store_true")
     ap.add_argument("--no-reorder", action="store_true", help="skip the shuffled-mesh reordering ablation")
     ap.add_argument("--no-modified", action="store_true", help="skip the modified-integration variants")
+    ap.add_argument("--no-colour", action="store_true", help="skip the colour-scatter ablation")
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -424,6 +425,20 @@ def main():
                     del ssp, su, sy
             except Exception as e:  # noqa: BLE001
                 variants["shuffled_reorder"] = {"unavailable": str(e).splitlines()[0]}
+        if not args.no_colour:
+            # scatter ablation: cells ordered by colour, one launch per colour without atomics
+            try:
+                csp = FemSpace(xyz, cells, kind="cg", degree=p, device=local, scatter="colour")
+                ncol = len(csp.colour_starts()) - 1
+                for prec, u_, y_ in (("fp64", u64, y64), ("fp32", u32, y32)):
+                    msv = time_steps(torch, lambda: csp.apply(u_, prec=prec, out=y_), vsteps, 2, flush, stream,
+                                     barrier)
+                    t = float(np.mean(msv))
+                    variants[f"colour_scatter_{prec}"] = {**tstat(msv), "gdofs": N / (t * 1e-3) / 1e9, "ms": t,
+                                                          "colours": ncol, "rel_l2_vs_fp64": rel(y_)}
+                del csp
+            except Exception as e:  # noqa: BLE001
+                variants["colour_scatter"] = {"unavailable": str(e).splitlines()[0]}
         if not args.no_modified:
             # Sec. 3.3: cell rule exact to degree 2p - 2 (15 instead of 35 points at p = 3); with a
             # constant coefficient the operator is the same (the integrand has degree 2p - 2)

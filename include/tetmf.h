@@ -82,6 +82,12 @@ extern "C" {
 #define FEM_REORDER_NONE 0
 #define FEM_REORDER_MORTON 1
 
+/* scatter of the CG FP64/FP32 apply and adjoint */
+#define FEM_SCATTER_ATOMIC 0  /* atomic adds (default)                           */
+#define FEM_SCATTER_COLOUR 1  /* cells ordered by colour (no two cells of one    */
+                              /* colour share a DoF), one launch per colour with */
+                              /* plain adds: bitwise reproducible results        */
+
 /* cell quadrature (face integrals always use the standard rule) */
 #define FEM_RULE_STANDARD 0  /* Grundmann-Moeller s = p: exact to degree 2p+1      */
 #define FEM_RULE_MODIFIED 1  /* s = p-1: exact to degree 2p-1 >= 2p-2, the degree */
@@ -112,6 +118,9 @@ typedef struct {
   int32_t device;            /* CUDA device ordinal; -1 builds a host-only   */
                              /* plan: queries work, hot calls return EINVAL  */
   int32_t cell_rule;         /* FEM_RULE_STANDARD (0) or FEM_RULE_MODIFIED   */
+  int32_t scatter;           /* FEM_SCATTER_ATOMIC (0) or FEM_SCATTER_COLOUR */
+                             /* (CG only; tensor-core precisions and the     */
+                             /* other hot calls keep atomic adds)            */
 } fem_space_desc;
 
 /* ---- set-up (synchronous) ------------------------------------------ */
@@ -148,6 +157,11 @@ int fem_dof_permutation(const fem_ctx* ctx, int64_t* lib_to_canonical);
 /* CG only: keys[i][0..p-1] = sorted user vertex ids whose mean is the node of
  * library DoF i (vertex v_m of a cell repeated beta_m times).  Array N*p. */
 int fem_dof_keys(const fem_ctx* ctx, int32_t* keys);
+
+/* Colour mode: *n_colours = number of colours (0 in atomic mode) and, if
+ * starts is not NULL, starts[0..n_colours] = first library cell of each
+ * colour (colour k = cells [starts[k], starts[k+1])).  Host memory. */
+int fem_colours(const fem_ctx* ctx, int32_t* n_colours, int64_t* starts);
 
 /* xyz[i][0..2] = physical position of the node of library DoF i (the point
  * where its shape function is 1): sum_m beta_m x_m / p over the vertices x_m

@@ -16,6 +16,7 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "tetmf.h")
 FEM_OK, FEM_EINVAL, FEM_EMESH, FEM_EUNSUPPORTED, FEM_ECUDA, FEM_ENOTCONV, FEM_ENOMEM = range(7)
 FEM_CG, FEM_DG = 0, 1
 FEM_RULE_STANDARD, FEM_RULE_MODIFIED = 0, 1
+FEM_SCATTER_ATOMIC, FEM_SCATTER_COLOUR = 0, 1
 FEM_FP64, FEM_FP32, FEM_TF32, FEM_BF16, FEM_TF32X3 = 0, 1, 2, 3, 4
 FEM_REORDER_NONE, FEM_REORDER_MORTON = 0, 1
 FEM_SOLVE_FP64_PCG, FEM_SOLVE_IR_MIXED = 0, 1
@@ -38,7 +39,7 @@ class MeshDesc(ctypes.Structure):
 class SpaceDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("degree", ctypes.c_int32), ("dirichlet", ctypes.c_int32),
                 ("reorder", ctypes.c_int32), ("dg_penalty_factor", ctypes.c_double), ("device", ctypes.c_int32),
-                ("cell_rule", ctypes.c_int32)]
+                ("cell_rule", ctypes.c_int32), ("scatter", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -64,6 +65,7 @@ _SIGNATURES = {
     "fem_dof_permutation": [_P, _P],
     "fem_dof_keys": [_P, _P],
     "fem_dof_coordinates": [_P, _P],
+    "fem_colours": [_P, _P, _P],
     "fem_dirichlet_mask": [_P, _P],
     "fem_device_status": [_P, _P],
     "fem_apply": [_P, ctypes.c_int32, _P, _P, _P, _P],

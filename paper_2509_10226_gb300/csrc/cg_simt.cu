@@ -71,19 +71,22 @@ __device__ inline void gather(const int32_t* __restrict__ idx, const T* __restri
 
 // y = A(k) u, Eq. 3.  The adjoint A(k)^T g is the same chain with D_e^T; the
 // stored metric is symmetric, so D_e^T = D_e and the same kernel serves both.
-template <int ND, int NQ, typename T>
+// COLOUR: the launch covers the cells [lo, hi) of one colour (tiles from lo / 128 on), no two
+// of which share a DoF, and adds to y without atomics.
+template <int ND, int NQ, typename T, bool COLOUR>
 __global__ void __launch_bounds__(kT) k_cg_apply(const int32_t* __restrict__ idx, const T* __restrict__ metric,
                                                  const T* __restrict__ tabE, const T* __restrict__ tabW,
                                                  const T* __restrict__ u, T* __restrict__ y,
-                                                 const T* __restrict__ kcoef, int64_t nc) {
+                                                 const T* __restrict__ kcoef, int64_t nc, int64_t lo, int64_t hi) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Shared<T> s = load_tables<ND, NQ, T>(smem, tabE, tabW, nullptr, false, kcoef != nullptr, false);
-  const int64_t tile = blockIdx.x;
+  const int64_t tile = (COLOUR ? lo / kT : 0) + blockIdx.x;
   const int64_t cell0 = tile * kT;
   if (kcoef) load_coeff_tile<NQ, T>(s.k, kcoef, cell0, nc);
   __syncthreads();
   const int lane = threadIdx.x;
   if (cell0 + lane >= nc) return;
+  if (COLOUR && (cell0 + lane < lo || cell0 + lane >= hi)) return;
 
   int g[ND];
   T ue[ND], ye[ND];
@@ -113,7 +116,10 @@ __global__ void __launch_bounds__(kT) k_cg_apply(const int32_t* __restrict__ idx
   }
 #pragma unroll
   for (int j = 0; j < ND; ++j)
-    if (g[j] >= 0) atomicAdd(y + g[j], ye[j]);
+    if (g[j] >= 0) {
+      if constexpr (COLOUR) y[g[j]] += ye[j];
+      else atomicAdd(y + g[j], ye[j]);
+    }
 }
 
 // Backward of L = <g, A(k) u>: grad_u = A(k)^T g and dk_{e,q} = w_q gu^T M_e gg
@@ -251,9 +257,23 @@ int launch_apply(Ctx& c, const T* u, T* y, const T* k, const T* metric, const T*
   const TableLayout L = tables_layout(c.tab);
   if (int e = init_rows<T>(y, u, c.d_mask, c.ndofs, T(0), st)) return e;
   const size_t sm = smem_bytes<ND, NQ, T>(k != nullptr, false);
-  if (int e = allow_smem(k_cg_apply<ND, NQ, T>, sm)) return e;
-  k_cg_apply<ND, NQ, T><<<unsigned(c.ntiles), kT, sm, st>>>(c.d_idx, metric, tab + L.E, tab + L.w, u, y, k, c.nc);
-  TETMF_LAUNCH_CK();
+  if (c.colour_start.empty()) {
+    if (int e = allow_smem(k_cg_apply<ND, NQ, T, false>, sm)) return e;
+    k_cg_apply<ND, NQ, T, false><<<unsigned(c.ntiles), kT, sm, st>>>(c.d_idx, metric, tab + L.E, tab + L.w, u, y, k,
+                                                                    c.nc, 0, c.nc);
+    TETMF_LAUNCH_CK();
+    return FEM_OK;
+  }
+  // colour mode: one launch per colour, in colour order
+  if (int e = allow_smem(k_cg_apply<ND, NQ, T, true>, sm)) return e;
+  for (size_t col = 0; col + 1 < c.colour_start.size(); ++col) {
+    const int64_t lo = c.colour_start[col], hi = c.colour_start[col + 1];
+    if (hi <= lo) continue;
+    const int64_t tiles = (hi - 1) / kT - lo / kT + 1;
+    k_cg_apply<ND, NQ, T, true><<<unsigned(tiles), kT, sm, st>>>(c.d_idx, metric, tab + L.E, tab + L.w, u, y, k,
+                                                                c.nc, lo, hi);
+    TETMF_LAUNCH_CK();
+  }
   return FEM_OK;
 }
 

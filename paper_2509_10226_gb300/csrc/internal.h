@@ -33,6 +33,8 @@ void build_tables(int p, int s_cell, RefTables& t);
 struct Ctx {
   // plan
   int kind = FEM_CG, p = 1, nd = 4, nq = 5, nqf = 4, dirichlet = 0, reorder = 1, device = -1;
+  int scatter = 0;                  // FEM_SCATTER_ATOMIC / FEM_SCATTER_COLOUR
+  std::vector<int64_t> colour_start;  // colour k = library cells [start[k], start[k+1]) (colour mode)
   double penalty = 0.0;
   int64_t nv = 0, nc = 0, ndofs = 0, ntiles = 0;
   RefTables tab;

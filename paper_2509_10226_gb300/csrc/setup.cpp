@@ -106,6 +106,44 @@ double longest_edge(const double* xyz, const int32_t* cv) {
   return L;
 }
 
+// Colour the cells so that no two cells of one colour share a DoF (greedy, lowest free colour,
+// cells visited in the current library order), then order the cells by colour, keeping the
+// order inside each colour.  The scatter of one colour then needs no atomics, and colours are
+// added one after the other: a deterministic summation order for every DoF.
+void colour_cells(Ctx& c) {
+  const int64_t nc = c.nc, N = c.ndofs;
+  const int nd = c.nd;
+  constexpr int kWords = 4;  // up to 256 colours
+  std::vector<uint64_t> used(size_t(N) * kWords, 0);
+  std::vector<int32_t> colour(nc);
+  int ncol = 0;
+  for (int64_t e = 0; e < nc; ++e) {
+    uint64_t busy[kWords] = {0, 0, 0, 0};
+    for (int j = 0; j < nd; ++j)
+      for (int w = 0; w < kWords; ++w) busy[w] |= used[size_t(c.cell_dofs[size_t(e) * nd + j]) * kWords + w];
+    int col = 0;
+    while (col < 64 * kWords && ((busy[col / 64] >> (col % 64)) & 1u)) ++col;
+    colour[e] = col;  // < 256: a cell shares DoFs with far fewer cells on any mesh this library accepts
+    ncol = std::max(ncol, col + 1);
+    for (int j = 0; j < nd; ++j) used[size_t(c.cell_dofs[size_t(e) * nd + j]) * kWords + col / 64] |= uint64_t(1) << (col % 64);
+  }
+  std::vector<int64_t> order(nc);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return colour[a] < colour[b]; });
+  c.colour_start.assign(ncol + 1, 0);
+  for (int64_t e = 0; e < nc; ++e) ++c.colour_start[colour[e] + 1];
+  for (int k = 0; k < ncol; ++k) c.colour_start[k + 1] += c.colour_start[k];
+  auto permute = [&](auto& v, int width) {
+    auto old = v;
+    for (int64_t i = 0; i < nc; ++i)
+      for (int r = 0; r < width; ++r) v[size_t(i) * width + r] = old[size_t(order[i]) * width + r];
+  };
+  permute(c.cell_perm, 1);
+  permute(c.cell_dofs, nd);
+  permute(c.metric, 6);
+  permute(c.absdet, 1);
+}
+
 int build_plan(Ctx& c, const fem_mesh_desc* m) {
   const double* xyz = m->xyz;
   const int32_t* ucells = m->cells;
@@ -424,6 +462,7 @@ int build_plan(Ctx& c, const fem_mesh_desc* m) {
       for (int r = 0; r < 5; ++r) c.fb_geo[size_t(r) * c.nfb + i] = g5[r];
     }
   }
+  if (c.kind == FEM_CG && c.scatter == FEM_SCATTER_COLOUR) colour_cells(c);
   c.ntiles = (nc + kTile - 1) / kTile;
   return FEM_OK;
 }
@@ -482,6 +521,14 @@ int fem_create(const fem_mesh_desc* mesh, const fem_space_desc* space, fem_ctx**
     set_error("fem_create: dirichlet must be 0 or 1");
     return FEM_EINVAL;
   }
+  if (space->scatter != FEM_SCATTER_ATOMIC && space->scatter != FEM_SCATTER_COLOUR) {
+    set_error("fem_create: scatter must be FEM_SCATTER_ATOMIC or FEM_SCATTER_COLOUR");
+    return FEM_EINVAL;
+  }
+  if (space->scatter == FEM_SCATTER_COLOUR && space->kind != FEM_CG) {
+    set_error("fem_create: FEM_SCATTER_COLOUR is offered for CG spaces");
+    return FEM_EINVAL;
+  }
   if (space->cell_rule != FEM_RULE_STANDARD && space->cell_rule != FEM_RULE_MODIFIED) {
     set_error("fem_create: cell_rule must be FEM_RULE_STANDARD or FEM_RULE_MODIFIED");
     return FEM_EINVAL;
@@ -500,6 +547,7 @@ int fem_create(const fem_mesh_desc* mesh, const fem_space_desc* space, fem_ctx**
   c.p = space->degree;
   c.dirichlet = space->dirichlet;
   c.reorder = space->reorder;
+  c.scatter = space->scatter;
   c.device = space->device;
   c.penalty = space->dg_penalty_factor > 0 ? space->dg_penalty_factor : double((c.p + 1) * (c.p + 3));
   c.nv = mesh->n_vertices;
@@ -587,6 +635,16 @@ int fem_dof_keys(const fem_ctx* ctx, int32_t* keys) {
   if (!keys) return set_error("null output"), FEM_EINVAL;
   if (ctx->c.kind != FEM_CG) return set_error("fem_dof_keys: CG spaces only"), FEM_EINVAL;
   std::memcpy(keys, ctx->c.dof_keys.data(), sizeof(int32_t) * ctx->c.dof_keys.size());
+  return FEM_OK;
+}
+
+int fem_colours(const fem_ctx* ctx, int32_t* n_colours, int64_t* starts) {
+  if (int s = check_ctx(ctx)) return s;
+  if (!n_colours) return set_error("null output"), FEM_EINVAL;
+  const Ctx& c = ctx->c;
+  *n_colours = c.colour_start.empty() ? 0 : int32_t(c.colour_start.size() - 1);
+  if (starts && !c.colour_start.empty())
+    std::memcpy(starts, c.colour_start.data(), sizeof(int64_t) * c.colour_start.size());
   return FEM_OK;
 }
 

@@ -35,18 +35,20 @@ class FemSpace:
 
     xyz [nv, 3] float64 and cells [nc, 4] int32 are host arrays in the user's
     numbering.  device = -1 builds a host-only plan (queries only).  modified_rule selects the
-    cell rule exact to degree 2p - 2 (Sec. 3.3; faces keep the standard rule).
+    cell rule exact to degree 2p - 2 (Sec. 3.3; faces keep the standard rule).  scatter = "colour"
+    (CG) orders the cells by colour and adds without atomics in the FP64/FP32 apply (reproducible).
     """
 
     def __init__(self, xyz, cells, kind="cg", degree=1, dirichlet=False, reorder=True, penalty=None, device=0,
-                 modified_rule=False):
+                 modified_rule=False, scatter="atomic"):
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int32)
         mesh = _lib.MeshDesc(xyz.shape[0], xyz.ctypes.data, cells.shape[0], cells.ctypes.data)
         space = _lib.SpaceDesc(_lib.FEM_CG if kind == "cg" else _lib.FEM_DG, int(degree), int(bool(dirichlet)),
                                _lib.FEM_REORDER_MORTON if reorder else _lib.FEM_REORDER_NONE,
                                float(penalty) if penalty else 0.0, int(device),
-                               _lib.FEM_RULE_MODIFIED if modified_rule else _lib.FEM_RULE_STANDARD)
+                               _lib.FEM_RULE_MODIFIED if modified_rule else _lib.FEM_RULE_STANDARD,
+                               _lib.FEM_SCATTER_COLOUR if scatter == "colour" else _lib.FEM_SCATTER_ATOMIC)
         h = ctypes.c_void_p()
         call("fem_create", ctypes.byref(mesh), ctypes.byref(space), ctypes.byref(h))
         self._h = h
@@ -94,6 +96,15 @@ class FemSpace:
     def dof_keys(self):
         out = np.empty((self.n_dofs, self.degree), dtype=np.int32)
         call("fem_dof_keys", self._h, out.ctypes.data)
+        return out
+
+    def colour_starts(self):
+        """First library cell of each colour and the end ([n_colours + 1]); empty in atomic mode."""
+        n = ctypes.c_int32()
+        call("fem_colours", self._h, ctypes.byref(n), None)
+        out = np.empty(n.value + 1 if n.value else 0, dtype=np.int64)
+        if n.value:
+            call("fem_colours", self._h, ctypes.byref(n), out.ctypes.data)
         return out
 
     def dof_coordinates(self):

@@ -250,3 +250,24 @@ def test_config4_p2_32cubed_variable_k_backward(prec):
             km[e] -= 1e-6
             fd = ((sp.apply(ud.detach(), k=kp) - sp.apply(ud.detach(), k=km)) @ wd).item() / 2e-6
         assert abs(fd - kd.grad[e].item()) <= 1e-8 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("p", [2, 3])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_colour_scatter_parity_and_reproducibility(p, prec):
+    """Colour mode: parity with the oracle, and bitwise-identical results over repeated applies
+    (the atomic mode is not bitwise reproducible in general)."""
+    from paper_2509_10226_gb300.fem import FemSpace
+
+    xyz, cells = synth.kuhn_cube(8, jitter=0.2, seed=2)
+    sp = FemSpace(xyz, cells, kind="cg", degree=p, device=0, scatter="colour")
+    dofs, keys = topology.cg_numbering(cells, p)
+    perm = sp.dof_permutation()
+    u = synth.uniform_vector(sp.n_dofs, 1)
+    ud = to_dev(u[perm], prec)
+    y0 = sp.apply(ud, prec=prec).clone()
+    assert_close(to_host(y0), cg.apply(xyz, cells, u, p, dofs=dofs)[perm], prec, "colour")
+    for _ in range(5):
+        assert torch.equal(sp.apply(ud, prec=prec), y0)
+    g = sp.apply_adjoint(ud, prec=prec)
+    assert torch.equal(g, y0)

@@ -82,6 +82,23 @@ def test_dof_coordinates(p):
     assert np.allclose(sp.dof_coordinates(), expect, rtol=0, atol=1e-14)
 
 
+@pytest.mark.parametrize("p", [1, 3])
+def test_colouring_is_valid(p):
+    """Colour mode: the colour ranges cover every library cell once and no two cells of one colour
+    share a global DoF (checked with the oracle's numbering of the user cells)."""
+    xyz, cells = synth.kuhn_cube(4, jitter=0.2, seed=3)
+    sp = space(xyz, cells, degree=p, scatter="colour")
+    starts = sp.colour_starts()
+    assert starts[0] == 0 and starts[-1] == cells.shape[0] and np.all(np.diff(starts) > 0)
+    dofs, _ = topology.cg_numbering(cells, p)
+    cperm = sp.cell_permutation()
+    for k in range(len(starts) - 1):
+        d = dofs[cperm[starts[k]:starts[k + 1]]].ravel()
+        assert np.unique(d).size == d.size, f"colour {k} shares a DoF"
+    assert len(starts) - 1 < 256
+    assert space(xyz, cells, degree=p).colour_starts().size == 0
+
+
 def test_morton_reorder_improves_locality():
     """Reordering a shuffled mesh makes the cells of a 128-cell batch share vertices (Sec. 2.5)."""
     xyz, cells = synth.kuhn_cube(8, jitter=0.2, seed=0)
