@@ -176,6 +176,19 @@ def time_steps(torch, fn, steps, warmup, flush, stream, barrier):
     return [a.elapsed_time(b) for a, b in ev]
 
 
+def replica_max(x, dist, device):
+    """Max of a per-rank value over the replicas (the job's time is its slowest rank's); x itself
+    when there is no process group.  Replicas run the whole workload each, so the job's throughput is
+    world x units / replica_max(time)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def tstat(ms):
     """Median and minimum of per-step times (ms), next to the mean each line reports."""
     return {"ms_median": float(np.median(ms)), "ms_min": float(np.min(ms))}
@@ -302,11 +315,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(x, dist, "cuda")
 
     from paper_2509_10226_gb300.fem import FemSpace
 
