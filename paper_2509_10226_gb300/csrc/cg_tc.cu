@@ -23,16 +23,18 @@
 // gather requests than one per (cell, node) (the masked gather and the
 // scatter of Sec. 2.4).
 //
-// One CTA of 128 threads owns one TMEM lane per cell and loops over tiles:
+// A warpgroup of 128 threads owns one TMEM lane per cell and loops over tiles:
 //   1. build row m of U' from the staged values, write it to shared memory;
-//   2. one thread issues GEMM 1 (D in TMEM), commits to an mbarrier; the CTA
-//      starts copying the next tile's list, indices and metric (cp.async);
+//   2. one thread issues GEMM 1 (D in TMEM), commits to an mbarrier; meanwhile
+//      the previous tile is scattered (step 5); then the warpgroup starts
+//      copying the values of the tile after next and the list and node
+//      indices of the one after that (cp.async, a ring of four stages);
 //   3. each thread reads its row of G from TMEM in chunks of 16 points,
 //      applies the metric in FP32 and writes Q back into TMEM (tcgen05.st);
-//   4. one thread issues GEMM 2 with A = Q in TMEM; the CTA starts the next
-//      tile's value gather;
+//   4. one thread issues GEMM 2 with A = Q in TMEM; it runs while the next
+//      tile's rows are built;
 //   5. each thread reads its row of Y', pre-reduces it into shared memory,
-//      and the CTA adds the tile's distinct values to y with atomics.
+//      and the warpgroup adds the tile's distinct values to y with atomics.
 // Every wait on an MMA completion is bounded (about 1 s); on time-out the
 // kernel records bit 0 in the status word and stops after freeing its TMEM.
 //
@@ -60,8 +62,10 @@ constexpr int kT = kTile;
 
 
 
-// per-tile staging buffers: a ring of kStages per warpgroup (tile t, gather of t+1, metadata of t+2)
-constexpr int kStages = 3;
+// per-tile staging buffers: a ring of stages per warpgroup.  Four stages (tile t, values of t+1, values
+// of t+2 in flight, tile t-1 being flushed and then the metadata of t+3) where TMEM keeps a CTA below
+// four warpgroups, so that shared memory is left over; three (tile t, values of t+1 in flight, tile
+// t-1 and then the metadata of t+2) where four warpgroups fit, which need the shared memory.
 template <int ND, int NQ, bool HAS_K>
 struct Stage {
   uint32_t* lidx;   // [NDP / 2][128] pairs of 16-bit list positions (node 2w low, 2w+1 high)
@@ -134,6 +138,10 @@ template <int ND, int NQ, bool BF16, bool X3>
 constexpr int tc_max_groups() {
   return 512 / tc_tcols<ND, NQ, BF16, X3>() < 4 ? 512 / tc_tcols<ND, NQ, BF16, X3>() : 4;
 }
+template <int ND, int NQ, bool BF16, bool X3>
+constexpr int tc_stages() {
+  return tc_max_groups<ND, NQ, BF16, X3>() < 4 ? 4 : 3;
+}
 
 template <int ND, int NQ, bool BF16, bool HAS_K, bool X3>
 __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3>(), 1)
@@ -164,6 +172,8 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3>(), 1)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 8);       // warpgroup 0's slot
   uint32_t* wmax = reinterpret_cast<uint32_t*>(misc + 32 * g + 16);  // per-warp maxima
   const size_t sbytes = stage_bytes<ND, NQ, HAS_K>(lmax);
+  constexpr int kStages = tc_stages<ND, NQ, BF16, X3>();
+  constexpr int D = kStages - 2;  // gather distance: values of tile t + D are copied during tile t
   uint8_t* stage_base = misc + 32 * G + size_t(g) * kStages * sbytes;
   auto stage = [&](int i) { return stage_at<ND, NQ, HAS_K>(stage_base + size_t(i) * sbytes, lmax); };
 
@@ -179,12 +189,13 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3>(), 1)
                  "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // Prefetch ring of kStages = 3 stages per warpgroup.  Commit order of cp.async groups: during tile t
-  // the gather of tile t+1, then the metadata of tile t+2 (empty groups past the last tile), so
-  // "wait_group 1" completes the gather of t+1 and "wait_group 0" the metadata of t+1.
+  // Prefetch ring.  During tile t the gather of tile t+D and the metadata of tile t+D+1 are issued
+  // (empty groups past the last tile).  D = 2: both are awaited during tile t+1, before its GEMM 1
+  // completes, so a gather has about one tile of time to arrive.  D = 1: the metadata is awaited
+  // there and the gather at the end of tile t.
   const int64_t stride = int64_t(gridDim.x) * G;
   int64_t tile = int64_t(blockIdx.x) * G + g;
-  int L_cur = 0, L_next = 0;
+  int L_cur = 0, L_next = 0, L_next2 = 0;
   if (tile < ntiles)
     L_cur = issue_meta<ND, NQ, HAS_K>(stage(0), m, tile, tl_span, tl_list, tl_lidx, kcoef, nc);
   else
@@ -203,8 +214,19 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3>(), 1)
     L_next = issue_meta<ND, NQ, HAS_K>(stage(1), m, tile + stride, tl_span, tl_list, tl_lidx, kcoef, nc);
   else
     cp_async_commit();
-  cp_async_wait_group<1>();
-  wg_sync(g);
+  if constexpr (D == 2) {
+    cp_async_wait_group<0>();
+    wg_sync(g);
+    if (tile + stride < ntiles) issue_gather<ND, NQ, HAS_K>(stage(1), m, L_next, u);
+    else cp_async_commit();
+    if (tile + 2 * stride < ntiles)
+      L_next2 = issue_meta<ND, NQ, HAS_K>(stage(2), m, tile + 2 * stride, tl_span, tl_list, tl_lidx, kcoef, nc);
+    else
+      cp_async_commit();
+  } else {
+    cp_async_wait_group<1>();
+    wg_sync(g);
+  }
   uint32_t phase = 0;
   bool failed = false;
   int b = 0;
@@ -264,16 +286,16 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3>(), 1)
   };
 
   for (; tile < ntiles; tile += stride, b = (b + 1 == kStages ? 0 : b + 1)) {
-    const int b1 = b + 1 == kStages ? 0 : b + 1;
-    const int b2 = b1 + 1 == kStages ? 0 : b1 + 1;  // also the stage of tile t-1
+    const int bg = (b + D) % kStages;      // tile t+D: gather target
+    const int bm = (b + D + 1) % kStages;  // tile t-1 (flushed), then the metadata of t+D+1
     const St cur = stage(b);
-    const int64_t next = tile + stride, next2 = tile + 2 * stride;
+    const int64_t tg = tile + D * stride, tm = tile + (D + 1) * stride;
     // this cell's metric, consumed after GEMM 1 (coalesced loads, latency hidden by the row build)
     const float* mp = metric + tile * 6 * kT + m;
     const float m0 = __ldg(mp), m1 = __ldg(mp + kT), m2 = __ldg(mp + 2 * kT), m3 = __ldg(mp + 3 * kT),
                 m4 = __ldg(mp + 4 * kT), m5 = __ldg(mp + 5 * kT);
     const int L = L_cur;
-    int L_next2 = 0;
+    int L_new = 0;
     // 1. row m of U' from the staged values (difference form); node positions stay in registers
     uint32_t lw[NDP / 2];
 #pragma unroll
@@ -325,20 +347,20 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3>(), 1)
       mma_commit(bar_a);
     }
     for (int i = m; i < (L + 4) / 4; i += kT) reinterpret_cast<float4*>(cur.vals)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (have_prev) scatter(stage(b2), L_prev, lw_prev);
-    cp_async_wait_group<0>();  // this thread's share of the metadata of tile t+1 (issued one tile ago)
-    // one thread waits for GEMM 1; the barrier also publishes the metadata of tile t+1 and the end
-    // of tile t-1's flush (its stage is refilled next)
+    if (have_prev) scatter(stage(bm), L_prev, lw_prev);
+    cp_async_wait_group<0>();  // this thread's share of the metadata of t+D (and, D = 2, values of t+1)
+    // one thread waits for GEMM 1; the barrier also publishes the copies awaited above and the end of
+    // tile t-1's flush (its stage is refilled next)
     if (m == 0) failed |= !mbar_wait(bar_a, phase);
     phase ^= 1;
     failed = wg_any(g, failed);
     if (failed) break;
     tc_fence_after();
-    // gather of tile t+1, metadata of tile t+2
-    if (next < ntiles) issue_gather<ND, NQ, HAS_K>(stage(b1), m, L_next, u);
+    // gather of tile t+D, metadata of tile t+D+1
+    if (tg < ntiles) issue_gather<ND, NQ, HAS_K>(stage(bg), m, D == 2 ? L_next2 : L_next, u);
     else cp_async_commit();
-    if (next2 < ntiles)
-      L_next2 = issue_meta<ND, NQ, HAS_K>(stage(b2), m, next2, tl_span, tl_list, tl_lidx, kcoef, nc);
+    if (tm < ntiles)
+      L_new = issue_meta<ND, NQ, HAS_K>(stage(bm), m, tm, tl_span, tl_list, tl_lidx, kcoef, nc);
     else
       cp_async_commit();
     // 3. D_e per quadrature point: G in TMEM becomes Q = (k_q) M_e g_q (w_q is folded into the table of GEMM 2)
@@ -363,14 +385,19 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3>(), 1)
       }
       mma_commit(bar_a);
     }
-    cp_async_wait_group<1>();  // gather of tile t+1 (this thread's share; published by the next barrier)
     have_prev = true;
     L_prev = L;
 #pragma unroll
     for (int w = 0; w < NDP / 2; ++w) lw_prev[w] = lw[w];
     L_cur = L_next;
-    L_next = L_next2;
-    wg_sync(g);
+    if constexpr (D == 2) {
+      L_next = L_next2;
+      L_next2 = L_new;
+    } else {
+      L_next = L_new;
+      cp_async_wait_group<1>();  // gather of tile t+1 (this thread's share; published by the barrier)
+      wg_sync(g);
+    }
   }
   // the last tile's scatter
   if (have_prev && !failed) {
@@ -431,7 +458,7 @@ size_t tc_smem(int lmax, int G) {
   using S = TcShape<ND, NQ, BF16>;
   constexpr int NIMG = X3 ? 2 : 1;
   return size_t(NIMG) * (S::B1_BYTES + S::B2_BYTES) +
-         size_t(G) * (NIMG * S::A1_BYTES + 32 + kStages * stage_bytes<ND, NQ, HAS_K>(lmax));
+         size_t(G) * (NIMG * S::A1_BYTES + 32 + tc_stages<ND, NQ, BF16, X3>() * stage_bytes<ND, NQ, HAS_K>(lmax));
 }
 
 template <int ND, int NQ, bool BF16, bool X3>
