@@ -129,3 +129,25 @@ def test_too_small_modified_rule_is_caught(monkeypatch):
     monkeypatch.setattr(quadrature, "tet_rule", lambda p, modified=False: orig(p - 1 if modified else p, modified))
     with pytest.raises(AssertionError):
         test_modified_element_matrix_brute_force(3)
+
+
+def test_wrong_chebyshev_recurrence_is_caught(monkeypatch):
+    """rho_k = 1 / (2 sigma + rho_{k-1}) instead of 1 / (2 sigma - rho_{k-1}) fails the error-polynomial pin."""
+    from oracle import smoother
+    from tests.test_oracle_smoother import test_error_polynomial_on_a_diagonal_operator
+
+    test_error_polynomial_on_a_diagonal_operator(5)
+
+    def wrong(degree, lam_max, lam_min):
+        theta, delta = 0.5 * (lam_max + lam_min), 0.5 * (lam_max - lam_min)
+        sigma = theta / delta
+        out, rho = [(0.0, 1.0 / theta)], 1.0 / sigma
+        for _ in range(degree - 1):
+            rho_new = 1.0 / (2.0 * sigma + rho)
+            out.append((rho_new * rho, 2.0 * rho_new / delta))
+            rho = rho_new
+        return out
+
+    monkeypatch.setattr(smoother, "step_coefficients", wrong)
+    with pytest.raises(AssertionError):
+        test_error_polynomial_on_a_diagonal_operator(5)
