@@ -291,6 +291,7 @@ def main():
     ap.add_argument("--no-reorder", action="store_true", help="skip the shuffled-mesh reordering ablation")
     ap.add_argument("--no-modified", action="store_true", help="skip the modified-integration variants")
     ap.add_argument("--no-colour", action="store_true", help="skip the colour-scatter ablation")
+    ap.add_argument("--no-smoother", action="store_true", help="skip the Chebyshev smoother sweeps")
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -434,6 +435,23 @@ def main():
                     del ssp, su, sy
             except Exception as e:  # noqa: BLE001
                 variants["shuffled_reorder"] = {"unavailable": str(e).splitlines()[0]}
+        if not args.no_smoother:
+            # Chebyshev-Jacobi smoothing sweeps of degree 5 (the smoother of the paper's multigrid,
+            # Sec. 4.1) with the tensor-core apply: one apply and one fused vector pass per step
+            try:
+                sm = {}
+                for prec in ("tf32", "fp64"):
+                    uu, xx = (u64, y64) if prec == "fp64" else (u32, y32)
+                    dg_ = sp.diagonal(prec=prec)
+                    lam = 1.2 * sp.lambda_max(dg_, uu, iterations=20, prec=prec)
+                    msv = time_steps(torch, lambda: sp.chebyshev(uu, xx, dg_, degree=5, lam_max=lam, prec=prec),
+                                     vsteps if prec != "fp64" else 5, 2, flush, stream, barrier)
+                    t = float(np.mean(msv))
+                    sm[prec] = {**tstat(msv), "ms_per_sweep": t, "applies_per_sweep": 5,
+                                "gdofs_per_apply": 5 * N / (t * 1e-3) / 1e9, "lambda_max": lam}
+                variants["chebyshev_degree5"] = sm
+            except Exception as e:  # noqa: BLE001
+                variants["chebyshev_degree5"] = {"unavailable": str(e).splitlines()[0]}
         if not args.no_colour:
             # scatter ablation: cells ordered by colour, one launch per colour without atomics
             try:

@@ -204,6 +204,35 @@ int fem_diagonal(fem_ctx* ctx, int32_t prec, void* d, const void* k, void* strea
 /* b_i = int f phi_i for a constant f (CG; FP64; Dirichlet entries 0). */
 int fem_rhs_const(fem_ctx* ctx, double f, double* b, void* stream);
 
+/* ---- smoother (Chebyshev-Jacobi, the smoother of Sec. 4.1's multigrid) */
+
+/* `degree` steps of Chebyshev iteration for A x = b preconditioned by
+ * D = diag(A), tuned to the interval [lam_max / ratio, lam_max] of the
+ * spectrum of D^-1 A: with theta, delta the centre and half width,
+ * sigma = theta / delta, d_0 = D^-1 r_0 / theta, rho_0 = 1 / sigma,
+ * rho_k = 1 / (2 sigma - rho_{k-1}),
+ * d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / delta) D^-1 r_k,
+ * x_{k+1} = x_k + d_k, r_k = b - A x_k.  x holds x_0 on entry and x_degree on
+ * return.  b, x, diag: device vectors of N (double for FEM_FP64, float
+ * otherwise; diag as fem_diagonal gives it, Dirichlet rows 1); the apply runs
+ * in `prec` (no coefficient).  work: device scratch of
+ * fem_smoother_work_bytes bytes.  Asynchronous, allocates nothing.  Errors:
+ * EINVAL (null pointer, degree < 1, lam_max <= 0, ratio <= 1), EUNSUPPORTED,
+ * ECUDA. */
+int fem_chebyshev(fem_ctx* ctx, int32_t prec, const void* b, void* x, const void* diag, int32_t degree,
+                  double lam_max, double ratio, void* work, void* stream);
+
+/* Largest eigenvalue of D^-1 A by `iterations` steps of power iteration from
+ * v0 (device, N values, not modified): v <- D^-1 A v / |D^-1 A v|_2, and
+ * *lam = (v, A v) / (v, D v) of the last iterate before its update.  work as
+ * for fem_chebyshev.  Blocking: reads three FP64 sums back every step
+ * (deterministic two-pass reductions). */
+int fem_lambda_max(fem_ctx* ctx, int32_t prec, const void* diag, const void* v0, int32_t iterations,
+                   void* work, double* lam, void* stream);
+
+/* Bytes of device scratch that fem_chebyshev and fem_lambda_max need. */
+int fem_smoother_work_bytes(const fem_ctx* ctx, int32_t prec, int64_t* bytes);
+
 /* ---- assembled comparator (Sec. 3.2) ------------------------------- */
 
 /* Assemble the same operator as a CSR matrix on the device (CG only;

@@ -487,6 +487,27 @@ int check_device(const fem_ctx* ctx) {
 }  // namespace
 }  // namespace tetmf
 
+namespace tetmf {
+// y = A u without a coefficient, in any precision the space offers (shared by the smoother)
+int apply_op(Ctx& c, int prec, const void* u, void* y, void* stream) {
+  if (c.kind == FEM_DG) {
+    if (prec == FEM_TF32 || prec == FEM_BF16) return dg_apply_tc(c, prec, u, y, stream);
+    if (prec != FEM_FP64 && prec != FEM_FP32) return set_error("precision %d not offered for DG", prec), FEM_EUNSUPPORTED;
+    return dg_apply(c, prec, u, y, stream);
+  }
+  switch (prec) {
+    case FEM_FP64:
+    case FEM_FP32:
+      return cg_apply_simt(c, prec, u, y, nullptr, false, stream);
+    case FEM_TF32:
+    case FEM_BF16:
+    case FEM_TF32X3:
+      return cg_apply_tc(c, prec, u, y, nullptr, stream);
+  }
+  return set_error("unknown precision %d", prec), FEM_EUNSUPPORTED;
+}
+}  // namespace tetmf
+
 using namespace tetmf;
 
 extern "C" {
@@ -691,6 +712,32 @@ int fem_device_status(fem_ctx* ctx, int32_t* status) {
   if (int s = check_device(ctx)) return s;
   if (!status) return set_error("null output"), FEM_EINVAL;
   return device_status(ctx->c, status);
+}
+
+int fem_chebyshev(fem_ctx* ctx, int32_t prec, const void* b, void* x, const void* diag, int32_t degree,
+                  double lam_max, double ratio, void* work, void* stream) {
+  if (int s = check_device(ctx)) return s;
+  if (!b || !x || !diag || !work) return set_error("fem_chebyshev: null pointer"), FEM_EINVAL;
+  if (degree < 1 || !(lam_max > 0.0) || !(ratio > 1.0))
+    return set_error("fem_chebyshev: need degree >= 1, lam_max > 0, ratio > 1"), FEM_EINVAL;
+  if (prec < FEM_FP64 || prec > FEM_TF32X3) return set_error("fem_chebyshev: unknown precision %d", prec), FEM_EUNSUPPORTED;
+  return chebyshev(ctx->c, prec, b, x, diag, degree, lam_max, lam_max / ratio, work, stream);
+}
+
+int fem_lambda_max(fem_ctx* ctx, int32_t prec, const void* diag, const void* v0, int32_t iterations, void* work,
+                   double* lam, void* stream) {
+  if (int s = check_device(ctx)) return s;
+  if (!diag || !v0 || !work || !lam) return set_error("fem_lambda_max: null pointer"), FEM_EINVAL;
+  if (iterations < 1) return set_error("fem_lambda_max: iterations >= 1"), FEM_EINVAL;
+  if (prec < FEM_FP64 || prec > FEM_TF32X3) return set_error("fem_lambda_max: unknown precision %d", prec), FEM_EUNSUPPORTED;
+  return lambda_max(ctx->c, prec, diag, v0, iterations, work, lam, stream);
+}
+
+int fem_smoother_work_bytes(const fem_ctx* ctx, int32_t prec, int64_t* bytes) {
+  if (int s = check_ctx(ctx)) return s;
+  if (!bytes) return set_error("null output"), FEM_EINVAL;
+  *bytes = int64_t(lambda_max_work_bytes(ctx->c, prec));
+  return FEM_OK;
 }
 
 int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k, void* stream) {

@@ -182,6 +182,31 @@ class FemSpace:
         call("fem_csr_apply", self._h, PREC[prec], _ptr(u), _ptr(y), _stream(stream))
         return y
 
+    def _smoother_work(self, prec):
+        nb = ctypes.c_int64()
+        call("fem_smoother_work_bytes", self._h, PREC[prec], ctypes.byref(nb))
+        return torch.empty(nb.value, dtype=torch.uint8, device=f"cuda:{self.device}")
+
+    def chebyshev(self, b, x, diag, degree=5, lam_max=None, ratio=15.0, prec="fp64", stream=None):
+        """degree steps of Chebyshev-Jacobi smoothing of A x = b, x updated in place; lam_max bounds
+        the spectrum of diag^-1 A (see lambda_max)."""
+        for t, name in ((b, "b"), (x, "x"), (diag, "diag")):
+            self._check_vec(t, prec, name)
+        work = self._smoother_work(prec)
+        call("fem_chebyshev", self._h, PREC[prec], _ptr(b), _ptr(x), _ptr(diag), int(degree), float(lam_max),
+             float(ratio), _ptr(work), _stream(stream))
+        return x
+
+    def lambda_max(self, diag, v0, iterations=20, prec="fp64", stream=None):
+        """Power-iteration estimate of the largest eigenvalue of diag^-1 A (blocking)."""
+        self._check_vec(diag, prec, "diag")
+        self._check_vec(v0, prec, "v0")
+        work = self._smoother_work(prec)
+        lam = ctypes.c_double()
+        call("fem_lambda_max", self._h, PREC[prec], _ptr(diag), _ptr(v0), int(iterations), _ptr(work),
+             ctypes.byref(lam), _stream(stream))
+        return lam.value
+
     def solve(self, b, x0=None, mode="ir", inner_prec="fp32", rtol=1e-10, inner_rtol=1e-3, max_outer=50,
               max_inner=20000, stream=None, raise_on_notconv=True, no_alloc=False):
         """Solve A x = b (blocking).  Returns (x, stats dict).
