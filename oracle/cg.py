@@ -4,7 +4,8 @@
 
 E is the 3 nq x ndof table of reference gradients at the quadrature points
 (Eq. 4, row 3i+k holds d_k phi_j(x_i)).  D_e acts at each quadrature point q as
-described below Eq. 4: apply the inverse-transpose Jacobian J^-T (reference to
+described below Eq. 4 (on curved cells, Sec. 3.2, with the Jacobian of the second-order map taken
+at each point): apply the inverse-transpose Jacobian J^-T (reference to
 physical gradient), multiply by the quadrature weight times |det J| (and by the
 coefficient k_q when one is given), then apply J^-1.  J = [x1-x0 | x2-x0 | x3-x0]
 is built from the user's vertex order of each cell.
@@ -30,6 +31,15 @@ def geometry(xyz: np.ndarray, cells: np.ndarray):
     return J, det, Jinv
 
 
+def geometry_curved(nodes: np.ndarray, xq: np.ndarray):
+    """Per-point geometry of a second-order cell map x(x_hat) = sum_j X_j phi_j(x_hat), phi the P2
+    Lagrange basis and X_j [C, 10, 3] its nodes: J [C, nq, 3, 3] with J[c, q, :, k] = d x / d x_hat_k
+    at point q, det J [C, nq], J^-1 [C, nq, 3, 3]."""
+    G2 = basis.gradients(2, xq)  # [nq, 10, 3]
+    J = np.einsum("cjd,qjk->cqdk", np.asarray(nodes, dtype=np.float64), G2)
+    return J, np.linalg.det(J), np.linalg.inv(J)
+
+
 def tables(p: int, modified: bool = False):
     """(x_hat [nq,3], w [nq], E as grad table [nq, ndof, 3], values [nq, ndof]); modified selects the
     cell rule of Sec. 3.3."""
@@ -53,15 +63,27 @@ def _qp_operator(Jinv, det, wq, k, transpose=False):
     return D
 
 
-def element_apply(xyz, cells, ue, p, k=None, transpose=False, modified=False):
-    """Local products y_e = E^T D_e E u_e for every cell; ue [C, ndof] -> [C, ndof]."""
+def element_apply(xyz, cells, ue, p, k=None, transpose=False, modified=False, nodes=None):
+    """Local products y_e = E^T D_e E u_e for every cell; ue [C, ndof] -> [C, ndof].  With nodes
+    [C, 10, 3] the cells are curved (second-order map) and J^-T, |det J| are taken per point."""
     xq, wq, G, _ = tables(p, modified)
     C = ue.shape[0]
     out = np.empty_like(ue, dtype=np.float64)
     for s in range(0, C, CHUNK):
         e = slice(s, min(C, s + CHUNK))
-        _, det, Jinv = geometry(xyz, cells[e])
         grad_ref = np.einsum("qjk,cj->cqk", G, ue[e])            # E u_e
+        if nodes is not None:
+            _, detq, Jq = geometry_curved(nodes[e], xq)          # per point
+            scale = wq[None, :] * np.abs(detq)
+            if k is not None:
+                scale = scale * k[e]
+            # J^-T, then JxW (and k), then J^-1, point by point; D_q is symmetric, so the adjoint
+            # chain is the same
+            t = np.einsum("cqak,cqa->cqk", Jq, grad_ref) * scale[:, :, None]
+            t_ref = np.einsum("cqak,cqk->cqa", Jq, t)
+            out[e] = np.einsum("qjk,cqk->cj", G, t_ref)
+            continue
+        _, det, Jinv = geometry(xyz, cells[e])
         if not transpose:
             # D_e in the order stated below Eq. 4: J^-T, then JxW (and k), then J^-1
             grad_phys = np.einsum("cak,cqa->cqk", Jinv, grad_ref)  # J^-T g_hat
@@ -83,7 +105,7 @@ def _scatter(dofs, ye, n):
     return y
 
 
-def apply(xyz, cells, u, p, k=None, dirichlet_mask=None, dofs=None, modified=False):
+def apply(xyz, cells, u, p, k=None, dirichlet_mask=None, dofs=None, modified=False, nodes=None):
     """y = A(k) u in canonical numbering.
 
     With a Dirichlet mask P (True = constrained) the operator is P A P + (I - P):
@@ -93,7 +115,7 @@ def apply(xyz, cells, u, p, k=None, dirichlet_mask=None, dofs=None, modified=Fal
         dofs, _ = topology.cg_numbering(cells, p)
     u = np.asarray(u, dtype=np.float64)
     uu = u if dirichlet_mask is None else np.where(dirichlet_mask, 0.0, u)
-    y = _scatter(dofs, element_apply(xyz, cells, uu[dofs], p, k, modified=modified), u.shape[0])
+    y = _scatter(dofs, element_apply(xyz, cells, uu[dofs], p, k, modified=modified, nodes=nodes), u.shape[0])
     if dirichlet_mask is not None:
         y = np.where(dirichlet_mask, u, y)
     return y
@@ -131,7 +153,7 @@ def coeff_grad(xyz, cells, u, g, p, k=None, dofs=None, modified=False):
     return apply_adjoint(xyz, cells, g, p, k, dofs=dofs, modified=modified), dk
 
 
-def diagonal(xyz, cells, p, n, k=None, dirichlet_mask=None, dofs=None, modified=False):
+def diagonal(xyz, cells, p, n, k=None, dirichlet_mask=None, dofs=None, modified=False, nodes=None):
     """diag(A): sum over cells and quadrature points of (J^-T grad phi_i)^T k w |detJ| (J^-T grad phi_i)."""
     if dofs is None:
         dofs, _ = topology.cg_numbering(cells, p)
@@ -140,9 +162,14 @@ def diagonal(xyz, cells, p, n, k=None, dirichlet_mask=None, dofs=None, modified=
     de = np.empty((C, G.shape[1]))
     for s in range(0, C, CHUNK):
         e = slice(s, min(C, s + CHUNK))
-        _, det, Jinv = geometry(xyz, cells[e])
-        gp = np.einsum("cak,qja->cqjk", Jinv, G)  # physical gradient of each shape function
-        scale = wq[None, :] * np.abs(det)[:, None]
+        if nodes is not None:
+            _, detq, Jq = geometry_curved(nodes[e], xq)
+            gp = np.einsum("cqak,qja->cqjk", Jq, G)
+            scale = wq[None, :] * np.abs(detq)
+        else:
+            _, det, Jinv = geometry(xyz, cells[e])
+            gp = np.einsum("cak,qja->cqjk", Jinv, G)  # physical gradient of each shape function
+            scale = wq[None, :] * np.abs(det)[:, None]
         if k is not None:
             scale = scale * k[e]
         de[e] = np.einsum("cq,cqjk,cqjk->cj", scale, gp, gp)
@@ -152,13 +179,17 @@ def diagonal(xyz, cells, p, n, k=None, dirichlet_mask=None, dofs=None, modified=
     return d
 
 
-def rhs_const(xyz, cells, p, n, f=1.0, dirichlet_mask=None, dofs=None, modified=False):
+def rhs_const(xyz, cells, p, n, f=1.0, dirichlet_mask=None, dofs=None, modified=False, nodes=None):
     """b_i = sum_e sum_q w_q |det J| phi_i(x_q) f for a constant source f (Sec. 2.1 weak form)."""
     if dofs is None:
         dofs, _ = topology.cg_numbering(cells, p)
     xq, wq, _, V = tables(p, modified)
-    _, det, _ = geometry(xyz, cells)
-    be = f * np.abs(det)[:, None] * (wq @ V)[None, :]
+    if nodes is not None:
+        _, detq, _ = geometry_curved(nodes, xq)
+        be = f * (np.abs(detq) * wq[None, :]) @ V
+    else:
+        _, det, _ = geometry(xyz, cells)
+        be = f * np.abs(det)[:, None] * (wq @ V)[None, :]
     b = _scatter(dofs, be, n)
     if dirichlet_mask is not None:
         b = np.where(dirichlet_mask, 0.0, b)

@@ -5,13 +5,14 @@ coordinates and cell connectivity) and random vectors.  The oracle and the CUDA
 library each derive everything else (quadrature, basis, DoF numbering, geometry)
 on their own.
 """
-from .mesh import kuhn_cube, shuffle_mesh, jitter_interior
+from .mesh import curved_nodes, kuhn_cube, shuffle_mesh, jitter_interior
 from .vectors import uniform_vector, lognormal_coefficients, SEEDS
 
 __all__ = [
     "kuhn_cube",
     "shuffle_mesh",
     "jitter_interior",
+    "curved_nodes",
     "uniform_vector",
     "lognormal_coefficients",
     "SEEDS",

@@ -83,3 +83,20 @@ def shuffle_mesh(xyz: np.ndarray, cells: np.ndarray, seed: int):
     cperm = rng.permutation(cells.shape[0])
     new_cells = inv[cells[cperm]].astype(np.int32)
     return xyz[vperm].copy(), new_cells, cperm
+
+
+# Second-order geometry nodes of a cell: the ten points sum_a beta_a x_a / 2 over the multi-indices
+# beta in N^4, |beta| = 2, in lexicographic ascending order (relative to the cell's vertex order).
+_BETA2 = [b for b in itertools.product(range(3), repeat=4) if sum(b) == 2]
+
+
+def curved_nodes(xyz: np.ndarray, cells: np.ndarray, amplitude: float) -> np.ndarray:
+    """Geometry nodes [nc, 10, 3] of a curved version of the mesh: the straight cells' second-order
+    nodes moved by the smooth map x -> x + amplitude * sin(pi x) sin(pi y) sin(pi z) * (1, 1, 1),
+    which is the identity on the boundary of the unit cube (boundary faces stay flat, the domain
+    stays the unit cube) and is evaluated once per node (shared nodes coincide)."""
+    X = np.asarray(xyz, dtype=np.float64)[np.asarray(cells, dtype=np.int64)]  # [nc, 4, 3]
+    B = np.array(_BETA2, dtype=np.float64) / 2.0                              # [10, 4]
+    P = np.einsum("na,cad->cnd", B, X)
+    s = np.sin(np.pi * P[..., 0]) * np.sin(np.pi * P[..., 1]) * np.sin(np.pi * P[..., 2])
+    return P + amplitude * s[..., None]
