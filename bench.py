@@ -292,6 +292,7 @@ def main():
     ap.add_argument("--no-modified", action="store_true", help="skip the modified-integration variants")
     ap.add_argument("--no-colour", action="store_true", help="skip the colour-scatter ablation")
     ap.add_argument("--no-smoother", action="store_true", help="skip the Chebyshev smoother sweeps")
+    ap.add_argument("--no-curved", action="store_true", help="skip the curved-cell variants")
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -435,6 +436,31 @@ def main():
                     del ssp, su, sy
             except Exception as e:  # noqa: BLE001
                 variants["shuffled_reorder"] = {"unavailable": str(e).splitlines()[0]}
+        if not args.no_curved:
+            # curved cells (second-order geometry, Sec. 3.2): a metric per quadrature point, 35 x 6
+            # words per cell instead of 6 -- the memory-bound variant of the apply
+            try:
+                nodes = synth.curved_nodes(xyz, cells, 0.05)
+                csp = FemSpace(xyz, cells, kind="cg", degree=p, device=local, cell_nodes=nodes)
+                del nodes
+                cur = {}
+                yref = None
+                for prec, u_, y_ in (("fp64", u64, y64), ("fp32", u32, y32), ("tf32", u32, y32), ("bf16", u32, y32)):
+                    msv = time_steps(torch, lambda: csp.apply(u_, prec=prec, out=y_), vsteps if prec != "fp64" else 5,
+                                     2, flush, stream, barrier)
+                    t = float(np.mean(msv))
+                    vb = 8 if prec == "fp64" else 4
+                    b = C * (4 * nd + 6 * nq * vb) + 2 * vb * N
+                    gbs = b / (t * 1e-3) / 1e9
+                    if prec == "fp64":
+                        yref = y64.clone()
+                    relc = float(torch.linalg.norm(y_.double() - yref) / torch.linalg.norm(yref))
+                    cur[prec] = {**tstat(msv), "gdofs": N / (t * 1e-3) / 1e9, "ms": t, "algorithmic_bytes": b,
+                                 "hbm_gbs": gbs, "frac_hbm": gbs / peaks["hbm_gbs"], "rel_l2_vs_fp64": relc}
+                variants["curved_p3_64"] = cur
+                del csp
+            except Exception as e:  # noqa: BLE001
+                variants["curved_p3_64"] = {"unavailable": str(e).splitlines()[0]}
         if not args.no_smoother:
             # Chebyshev-Jacobi smoothing sweeps of degree 5 (the smoother of the paper's multigrid,
             # Sec. 4.1) with the tensor-core apply: one apply and one fused vector pass per step

@@ -106,6 +106,14 @@ typedef struct {
   const double* xyz;      /* [n_vertices][3]                                */
   int64_t n_cells;
   const int32_t* cells;   /* [n_cells][4] vertex ids, user vertex order     */
+  const double* cell_nodes; /* NULL (straight cells) or [n_cells][10][3]:   */
+                          /* second-order geometry nodes of each cell, the */
+                          /* points sum_a beta_a x_a / 2 (|beta| = 2, beta */
+                          /* lexicographic, user vertex order) moved onto  */
+                          /* the curved cell; the map x(x_hat) is their P2 */
+                          /* interpolant and J^-T, |det J| are taken at    */
+                          /* every quadrature point (Sec. 3.2).  CG only;  */
+                          /* nodes shared by cells must coincide.          */
 } fem_mesh_desc;
 
 typedef struct {

@@ -33,7 +33,7 @@ class FemError(RuntimeError):
 
 class MeshDesc(ctypes.Structure):
     _fields_ = [("n_vertices", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("n_cells", ctypes.c_int64),
-                ("cells", ctypes.c_void_p)]
+                ("cells", ctypes.c_void_p), ("cell_nodes", ctypes.c_void_p)]
 
 
 class SpaceDesc(ctypes.Structure):

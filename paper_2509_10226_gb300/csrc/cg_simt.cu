@@ -9,6 +9,8 @@
 // t = w_q k_q M_e g with the symmetric metric M_e = |det J| J^-1 J^-T, and
 // accumulates y_e += E_q^T t (3 nd FMAs); the gather G_e skips constrained
 // DoFs and the scatter G_e^T adds with atomics (Eq. 3).
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace tetmf {
@@ -73,11 +75,13 @@ __device__ inline void gather(const int32_t* __restrict__ idx, const T* __restri
 // stored metric is symmetric, so D_e^T = D_e and the same kernel serves both.
 // COLOUR: the launch covers the cells [lo, hi) of one colour (tiles from lo / 128 on), no two
 // of which share a DoF, and adds to y without atomics.
+// qmetric (curved cells, or null): [tiles][NQ][6][kT] metric per quadrature point instead of per cell.
 template <int ND, int NQ, typename T, bool COLOUR>
 __global__ void __launch_bounds__(kT) k_cg_apply(const int32_t* __restrict__ idx, const T* __restrict__ metric,
                                                  const T* __restrict__ tabE, const T* __restrict__ tabW,
                                                  const T* __restrict__ u, T* __restrict__ y,
-                                                 const T* __restrict__ kcoef, int64_t nc, int64_t lo, int64_t hi) {
+                                                 const T* __restrict__ kcoef, int64_t nc, int64_t lo, int64_t hi,
+                                                 const T* __restrict__ qmetric) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Shared<T> s = load_tables<ND, NQ, T>(smem, tabE, tabW, nullptr, false, kcoef != nullptr, false);
   const int64_t tile = (COLOUR ? lo / kT : 0) + blockIdx.x;
@@ -94,10 +98,15 @@ __global__ void __launch_bounds__(kT) k_cg_apply(const int32_t* __restrict__ idx
 #pragma unroll
   for (int j = 0; j < ND; ++j) ye[j] = T(0);
   const T* mp = metric + tile * 6 * kT + lane;
-  const T m0 = mp[0], m1 = mp[kT], m2 = mp[2 * kT], m3 = mp[3 * kT], m4 = mp[4 * kT], m5 = mp[5 * kT];
+  T m0 = mp[0], m1 = mp[kT], m2 = mp[2 * kT], m3 = mp[3 * kT], m4 = mp[4 * kT], m5 = mp[5 * kT];
+  const T* qm = qmetric ? qmetric + tile * NQ * 6 * kT + lane : nullptr;
 
 #pragma unroll 1
   for (int q = 0; q < NQ; ++q) {
+    if (qm) {
+      const T* p = qm + q * 6 * kT;
+      m0 = p[0], m1 = p[kT], m2 = p[2 * kT], m3 = p[3 * kT], m4 = p[4 * kT], m5 = p[5 * kT];
+    }
     const T* Eq = s.E + q * 3 * ND;
     T gx = T(0), gy = T(0), gz = T(0);
 #pragma unroll
@@ -186,7 +195,8 @@ __global__ void __launch_bounds__(kT) k_cg_coeff_grad(const int32_t* __restrict_
 template <int ND, int NQ, typename T>
 __global__ void __launch_bounds__(kT) k_cg_diag(const int32_t* __restrict__ idx, const T* __restrict__ metric,
                                                 const T* __restrict__ tabE, const T* __restrict__ tabW,
-                                                const T* __restrict__ kcoef, T* __restrict__ d, int64_t nc) {
+                                                const T* __restrict__ kcoef, T* __restrict__ d, int64_t nc,
+                                                const T* __restrict__ qmetric) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Shared<T> s = load_tables<ND, NQ, T>(smem, tabE, tabW, nullptr, false, kcoef != nullptr, false);
   const int64_t tile = blockIdx.x;
@@ -196,12 +206,17 @@ __global__ void __launch_bounds__(kT) k_cg_diag(const int32_t* __restrict__ idx,
   const int lane = threadIdx.x;
   if (cell0 + lane >= nc) return;
   const T* mp = metric + tile * 6 * kT + lane;
-  const T m0 = mp[0], m1 = mp[kT], m2 = mp[2 * kT], m3 = mp[3 * kT], m4 = mp[4 * kT], m5 = mp[5 * kT];
+  T m0 = mp[0], m1 = mp[kT], m2 = mp[2 * kT], m3 = mp[3 * kT], m4 = mp[4 * kT], m5 = mp[5 * kT];
+  const T* qm = qmetric ? qmetric + tile * NQ * 6 * kT + lane : nullptr;
   T de[ND];
 #pragma unroll
   for (int j = 0; j < ND; ++j) de[j] = T(0);
 #pragma unroll 1
   for (int q = 0; q < NQ; ++q) {
+    if (qm) {
+      const T* p = qm + q * 6 * kT;
+      m0 = p[0], m1 = p[kT], m2 = p[2 * kT], m3 = p[3 * kT], m4 = p[4 * kT], m5 = p[5 * kT];
+    }
     const T* Eq = s.E + q * 3 * ND;
     T c = s.w[q];
     if (kcoef) c *= s.k[lane * kstride(NQ) + q];
@@ -220,27 +235,45 @@ __global__ void __launch_bounds__(kT) k_cg_diag(const int32_t* __restrict__ idx,
   }
 }
 
-// b_i = f sum_e |det J_e| sum_q w_q phi_i(x_q)
+// b_i = f sum_e |det J_e| sum_q w_q phi_i(x_q); curved cells (qdet: [tiles][NQ][kT]):
+// b_i = f sum_e sum_q w_q |det J_q| phi_i(x_q)
 template <int ND, int NQ>
 __global__ void __launch_bounds__(kT) k_cg_rhs(const int32_t* __restrict__ idx, const double* __restrict__ absdet,
                                                const double* __restrict__ tabV, const double* __restrict__ tabW,
-                                               double f, double* __restrict__ b, int64_t nc) {
+                                               double f, double* __restrict__ b, int64_t nc,
+                                               const double* __restrict__ qdet) {
   __shared__ double sv[ND];
+  __shared__ double swv[NQ * ND];
   for (int j = threadIdx.x; j < ND; j += blockDim.x) {
     double acc = 0.0;
     for (int q = 0; q < NQ; ++q) acc = fma(tabW[q], tabV[q * ND + j], acc);
     sv[j] = acc;
   }
+  for (int i = threadIdx.x; i < NQ * ND; i += blockDim.x) swv[i] = tabW[i / ND] * tabV[i];
   __syncthreads();
   const int64_t tile = blockIdx.x;
   const int lane = threadIdx.x;
   const int64_t cell = tile * kT + lane;
   if (cell >= nc) return;
-  const double s = f * absdet[cell];
+  double be[ND];
+  if (qdet) {
+#pragma unroll
+    for (int j = 0; j < ND; ++j) be[j] = 0.0;
+    const double* dq = qdet + tile * NQ * kT + lane;
+    for (int q = 0; q < NQ; ++q) {
+      const double s = f * dq[q * kT];
+#pragma unroll
+      for (int j = 0; j < ND; ++j) be[j] = fma(s, swv[q * ND + j], be[j]);
+    }
+  } else {
+    const double s = f * absdet[cell];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) be[j] = s * sv[j];
+  }
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
     const int gj = __ldg(idx + (tile * ND + j) * kT + lane);
-    if (gj >= 0) atomicAdd(b + gj, s * sv[j]);
+    if (gj >= 0) atomicAdd(b + gj, be[j]);
   }
 }
 
@@ -254,13 +287,15 @@ size_t smem_bytes(bool with_k, bool with_dk) {
 
 template <int ND, int NQ, typename T>
 int launch_apply(Ctx& c, const T* u, T* y, const T* k, const T* metric, const T* tab, cudaStream_t st) {
+  const T* qmetric = std::is_same<T, double>::value ? reinterpret_cast<const T*>(c.d_qmetric64)
+                                                     : reinterpret_cast<const T*>(c.d_qmetric32);
   const TableLayout L = tables_layout(c.tab);
   if (int e = init_rows<T>(y, u, c.d_mask, c.ndofs, T(0), st)) return e;
   const size_t sm = smem_bytes<ND, NQ, T>(k != nullptr, false);
   if (c.colour_start.empty()) {
     if (int e = allow_smem(k_cg_apply<ND, NQ, T, false>, sm)) return e;
     k_cg_apply<ND, NQ, T, false><<<unsigned(c.ntiles), kT, sm, st>>>(c.d_idx, metric, tab + L.E, tab + L.w, u, y, k,
-                                                                    c.nc, 0, c.nc);
+                                                                    c.nc, 0, c.nc, qmetric);
     TETMF_LAUNCH_CK();
     return FEM_OK;
   }
@@ -271,7 +306,7 @@ int launch_apply(Ctx& c, const T* u, T* y, const T* k, const T* metric, const T*
     if (hi <= lo) continue;
     const int64_t tiles = (hi - 1) / kT - lo / kT + 1;
     k_cg_apply<ND, NQ, T, true><<<unsigned(tiles), kT, sm, st>>>(c.d_idx, metric, tab + L.E, tab + L.w, u, y, k,
-                                                                c.nc, lo, hi);
+                                                                c.nc, lo, hi, qmetric);
     TETMF_LAUNCH_CK();
   }
   return FEM_OK;
@@ -296,7 +331,10 @@ int launch_diag(Ctx& c, T* d, const T* k, const T* metric, const T* tab, cudaStr
   if (int e = init_rows<T>(d, nullptr, c.d_mask, c.ndofs, T(1), st)) return e;
   const size_t sm = smem_bytes<ND, NQ, T>(k != nullptr, false);
   if (int e = allow_smem(k_cg_diag<ND, NQ, T>, sm)) return e;
-  k_cg_diag<ND, NQ, T><<<unsigned(c.ntiles), kT, sm, st>>>(c.d_idx, metric, tab + L.E, tab + L.w, k, d, c.nc);
+  const T* qmetric = std::is_same<T, double>::value ? reinterpret_cast<const T*>(c.d_qmetric64)
+                                                     : reinterpret_cast<const T*>(c.d_qmetric32);
+  k_cg_diag<ND, NQ, T><<<unsigned(c.ntiles), kT, sm, st>>>(c.d_idx, metric, tab + L.E, tab + L.w, k, d, c.nc,
+                                                          qmetric);
   TETMF_LAUNCH_CK();
   return FEM_OK;
 }
@@ -306,7 +344,7 @@ int launch_rhs(Ctx& c, double f, double* b, cudaStream_t st) {
   const TableLayout L = tables_layout(c.tab);
   if (int e = init_rows<double>(b, nullptr, c.d_mask, c.ndofs, 0.0, st)) return e;
   k_cg_rhs<ND, NQ><<<unsigned(c.ntiles), kT, 0, st>>>(c.d_idx, c.d_absdet, c.d_tab64 + L.V, c.d_tab64 + L.w, f, b,
-                                                      c.nc);
+                                                      c.nc, c.d_qdet64);
   TETMF_LAUNCH_CK();
   return FEM_OK;
 }
@@ -325,6 +363,10 @@ int cg_apply_simt(Ctx& c, int prec, const void* u, void* y, const void* k, bool 
 
 int cg_coeff_grad(Ctx& c, int prec, const void* u, const void* g, const void* k, void* grad_u, void* dk,
                   void* stream) {
+  if (c.curved) {
+    set_error("fem_coeff_grad: curved cells are not offered");
+    return FEM_EUNSUPPORTED;
+  }
   cudaStream_t st = as_stream(stream);
   if (prec == FEM_FP64) {
     TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_coeff_grad<ND, NQ, double>(

@@ -134,22 +134,25 @@ constexpr int tc_tcols() {
   using S = TcShape<ND, NQ, BF16>;
   return X3 ? round_up(2 * S::N1 + S::N2, 16) : round_up(S::D2_COL + S::N2, 16);
 }
-template <int ND, int NQ, bool BF16, bool X3>
+// CURVED (metric per quadrature point, read during the metric step): at most two warpgroups, so
+// that each thread has the registers to keep a chunk's point metrics in flight.
+template <int ND, int NQ, bool BF16, bool X3, bool CURVED = false>
 constexpr int tc_max_groups() {
-  return 512 / tc_tcols<ND, NQ, BF16, X3>() < 4 ? 512 / tc_tcols<ND, NQ, BF16, X3>() : 4;
+  return CURVED ? (512 / tc_tcols<ND, NQ, BF16, X3>() < 2 ? 512 / tc_tcols<ND, NQ, BF16, X3>() : 2)
+                : (512 / tc_tcols<ND, NQ, BF16, X3>() < 4 ? 512 / tc_tcols<ND, NQ, BF16, X3>() : 4);
 }
-template <int ND, int NQ, bool BF16, bool X3>
+template <int ND, int NQ, bool BF16, bool X3, bool CURVED = false>
 constexpr int tc_stages() {
-  return tc_max_groups<ND, NQ, BF16, X3>() < 4 ? 4 : 3;
+  return tc_max_groups<ND, NQ, BF16, X3, CURVED>() < 4 ? 4 : 3;
 }
 
-template <int ND, int NQ, bool BF16, bool HAS_K, bool X3>
-__global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3>(), 1)
+template <int ND, int NQ, bool BF16, bool HAS_K, bool X3, bool CURVED>
+__global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3, CURVED>(), 1)
     k_cg_apply_tc(const int64_t* __restrict__ tl_span, const int32_t* __restrict__ tl_list,
                   const uint16_t* __restrict__ tl_lidx, const float* __restrict__ metric,
                   const uint8_t* __restrict__ bimg, const float* __restrict__ u, float* __restrict__ y,
                   const float* __restrict__ kcoef, int64_t nc, int64_t ntiles, int lmax, uint32_t tmem_cols,
-                  int32_t* __restrict__ status) {
+                  int32_t* __restrict__ status, const float* __restrict__ qmetric) {
   using S = TcShape<ND, NQ, BF16>;
   using St = Stage<ND, NQ, HAS_K>;
   static_assert(!(X3 && BF16), "3xTF32 splits TF32 operands");
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3>(), 1)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 8);       // warpgroup 0's slot
   uint32_t* wmax = reinterpret_cast<uint32_t*>(misc + 32 * g + 16);  // per-warp maxima
   const size_t sbytes = stage_bytes<ND, NQ, HAS_K>(lmax);
-  constexpr int kStages = tc_stages<ND, NQ, BF16, X3>();
+  constexpr int kStages = tc_stages<ND, NQ, BF16, X3, CURVED>();
   constexpr int D = kStages - 2;  // gather distance: values of tile t + D are copied during tile t
   uint8_t* stage_base = misc + 32 * G + size_t(g) * kStages * sbytes;
   auto stage = [&](int i) { return stage_at<ND, NQ, HAS_K>(stage_base + size_t(i) * sbytes, lmax); };
@@ -290,10 +293,14 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3>(), 1)
     const int bm = (b + D + 1) % kStages;  // tile t-1 (flushed), then the metadata of t+D+1
     const St cur = stage(b);
     const int64_t tg = tile + D * stride, tm = tile + (D + 1) * stride;
-    // this cell's metric, consumed after GEMM 1 (coalesced loads, latency hidden by the row build)
-    const float* mp = metric + tile * 6 * kT + m;
-    const float m0 = __ldg(mp), m1 = __ldg(mp + kT), m2 = __ldg(mp + 2 * kT), m3 = __ldg(mp + 3 * kT),
-                m4 = __ldg(mp + 4 * kT), m5 = __ldg(mp + 5 * kT);
+    // this cell's metric, consumed after GEMM 1 (coalesced loads, latency hidden by the row build);
+    // curved cells read one metric per point during the metric step instead
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, m5 = 0.f;
+    if constexpr (!CURVED) {
+      const float* mp = metric + tile * 6 * kT + m;
+      m0 = __ldg(mp), m1 = __ldg(mp + kT), m2 = __ldg(mp + 2 * kT), m3 = __ldg(mp + 3 * kT), m4 = __ldg(mp + 4 * kT),
+      m5 = __ldg(mp + 5 * kT);
+    }
     const int L = L_cur;
     int L_new = 0;
     // 1. row m of U' from the staged values (difference form); node positions stay in registers
@@ -364,7 +371,8 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3>(), 1)
     else
       cp_async_commit();
     // 3. D_e per quadrature point: G in TMEM becomes Q = (k_q) M_e g_q (w_q is folded into the table of GEMM 2)
-    metric_to_q<ND, NQ, BF16, HAS_K, X3>(lane_base, m0, m1, m2, m3, m4, m5, HAS_K ? cur.kt + m * KS : nullptr, QLO);
+    metric_to_q<ND, NQ, BF16, HAS_K, X3, CURVED>(lane_base, m0, m1, m2, m3, m4, m5, HAS_K ? cur.kt + m * KS : nullptr,
+                                                 QLO, CURVED ? qmetric + tile * NQ * 6 * kT + m : nullptr);
     tmem_wait_st();
     tc_fence_before();
     wg_sync(g);
@@ -453,12 +461,13 @@ std::vector<uint8_t> b_image(const RefTables& t) {
   return img;
 }
 
-template <int ND, int NQ, bool BF16, bool HAS_K, bool X3>
+template <int ND, int NQ, bool BF16, bool HAS_K, bool X3, bool CURVED>
 size_t tc_smem(int lmax, int G) {
   using S = TcShape<ND, NQ, BF16>;
   constexpr int NIMG = X3 ? 2 : 1;
   return size_t(NIMG) * (S::B1_BYTES + S::B2_BYTES) +
-         size_t(G) * (NIMG * S::A1_BYTES + 32 + tc_stages<ND, NQ, BF16, X3>() * stage_bytes<ND, NQ, HAS_K>(lmax));
+         size_t(G) * (NIMG * S::A1_BYTES + 32 +
+                      tc_stages<ND, NQ, BF16, X3, CURVED>() * stage_bytes<ND, NQ, HAS_K>(lmax));
 }
 
 template <int ND, int NQ, bool BF16, bool X3>
@@ -479,18 +488,18 @@ int prepare(Ctx& c) {
   return upload_image<ND, NQ, true, false>(c, &c.d_tc_bf16);
 }
 
-template <int ND, int NQ, bool BF16, bool HAS_K, bool X3>
+template <int ND, int NQ, bool BF16, bool HAS_K, bool X3, bool CURVED>
 int launch_g(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) {
   constexpr int TCOLS = tc_tcols<ND, NQ, BF16, X3>();
   const int lmax = round_up(c.tl_max + 1, 4);  // list + the zero slot
-  auto kern = k_cg_apply_tc<ND, NQ, BF16, HAS_K, X3>;
+  auto kern = k_cg_apply_tc<ND, NQ, BF16, HAS_K, X3, CURVED>;
   int dev = 0, smem_max = 0;
   TETMF_CK(cudaGetDevice(&dev));
   TETMF_CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   // warpgroups per CTA: as many tiles in flight per SM as TMEM (512 columns) and shared memory allow
-  int G = tc_max_groups<ND, NQ, BF16, X3>();
-  while (G > 1 && tc_smem<ND, NQ, BF16, HAS_K, X3>(lmax, G) > size_t(smem_max)) --G;
-  const size_t sm = tc_smem<ND, NQ, BF16, HAS_K, X3>(lmax, G);
+  int G = tc_max_groups<ND, NQ, BF16, X3, CURVED>();
+  while (G > 1 && tc_smem<ND, NQ, BF16, HAS_K, X3, CURVED>(lmax, G) > size_t(smem_max)) --G;
+  const size_t sm = tc_smem<ND, NQ, BF16, HAS_K, X3, CURVED>(lmax, G);
   if (G < 1 || sm > size_t(smem_max)) {
     set_error("tensor-core kernel does not fit on an SM (%zu bytes of shared memory)", sm);
     return FEM_EUNSUPPORTED;
@@ -502,7 +511,7 @@ int launch_g(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) 
   const void* img = X3 ? c.d_tc_tf32x3 : BF16 ? c.d_tc_bf16 : c.d_tc_tf32;
   kern<<<unsigned(grid), G * kT, sm, st>>>(c.d_tl_span, c.d_tl_list, c.d_tl_lidx, c.d_metric32,
                                            static_cast<const uint8_t*>(img), u, y, k, c.nc, c.ntiles, lmax, cols,
-                                           c.d_status);
+                                           c.d_status, c.d_qmetric32);
   TETMF_LAUNCH_CK();
   return FEM_OK;
 }
@@ -510,11 +519,22 @@ int launch_g(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) 
 template <int ND, int NQ, bool BF16, bool X3>
 int launch(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) {
   if (int e = init_rows<float>(y, u, c.d_mask, c.ndofs, 0.0f, st)) return e;
-  return k ? launch_g<ND, NQ, BF16, true, X3>(c, u, y, k, st) : launch_g<ND, NQ, BF16, false, X3>(c, u, y, k, st);
+  return k ? launch_g<ND, NQ, BF16, true, X3, false>(c, u, y, k, st)
+           : launch_g<ND, NQ, BF16, false, X3, false>(c, u, y, k, st);
 }
 
 template <int ND, int NQ>
 int launch_prec(Ctx& c, int prec, const float* u, float* y, const float* k, cudaStream_t st) {
+  if (c.curved) {
+    // curved cells: TF32 / BF16 without a coefficient
+    if (k || (prec != FEM_TF32 && prec != FEM_BF16)) {
+      set_error("curved cells on the tensor cores: FEM_TF32 or FEM_BF16 without a coefficient");
+      return FEM_EUNSUPPORTED;
+    }
+    if (int e = init_rows<float>(y, u, c.d_mask, c.ndofs, 0.0f, st)) return e;
+    return prec == FEM_BF16 ? launch_g<ND, NQ, true, false, false, true>(c, u, y, k, st)
+                            : launch_g<ND, NQ, false, false, false, true>(c, u, y, k, st);
+  }
   if (prec == FEM_BF16) return launch<ND, NQ, true, false>(c, u, y, k, st);
   if (prec == FEM_TF32X3) {
     if constexpr (ND > 20) {

@@ -197,6 +197,10 @@ int spmv(Ctx& c, const T* u, T* y, const T* val, cudaStream_t st) {
 }  // namespace
 
 int csr_build(Ctx& c, int64_t* nnz) {
+  if (c.curved) {
+    set_error("fem_csr_build: the assembled comparator is built for straight cells only");
+    return FEM_EUNSUPPORTED;
+  }
   if (c.d_csr_rowptr) {
     if (nnz) *nnz = c.csr_nnz;
     return FEM_OK;

@@ -128,6 +128,22 @@ int upload(Ctx& c) {
   if (int s = put(c, &c.d_metric64, met)) return s;
   if (int s = put(c, &c.d_metric32, cast<float>(met))) return s;
   if (int s = put(c, &c.d_absdet, c.absdet)) return s;
+  if (c.curved) {
+    // [ntiles][nq][6][kTile] and [ntiles][nq][kTile]: coalesced per point inside a tile
+    const int nq = c.nq;
+    std::vector<double> qm(ncp * nq * 6, 0.0), qd(ncp * nq, 0.0);
+    for (int64_t e = 0; e < c.nc; ++e) {
+      const int64_t t = e / T, l = e % T;
+      for (int q = 0; q < nq; ++q) {
+        for (int a = 0; a < 6; ++a)
+          qm[((size_t(t) * nq + q) * 6 + a) * T + l] = c.qmetric[(size_t(e) * nq + q) * 6 + a];
+        qd[(size_t(t) * nq + q) * T + l] = c.qdet[size_t(e) * nq + q];
+      }
+    }
+    if (int s = put(c, &c.d_qmetric64, qm)) return s;
+    if (int s = put(c, &c.d_qmetric32, cast<float>(qm))) return s;
+    if (int s = put(c, &c.d_qdet64, qd)) return s;
+  }
 
   const TableLayout L = tables_layout(c.tab);
   std::vector<double> tab(L.total);

@@ -24,6 +24,7 @@ struct RefTables {
   std::vector<double> Vf;     // [4][nqf][nd] values at face points of local face m
   std::vector<double> Ef;     // [4][nqf][3][nd] reference gradients there
   std::vector<int32_t> fperm; // [6][nqf] face point index seen from the other side
+  std::vector<double> G2;     // [nq][3][10] reference gradients of the second-order geometry basis
 };
 
 // cell rule: Grundmann-Moeller with s = s_cell (p, or p - 1 for the modified integration of
@@ -47,6 +48,9 @@ struct Ctx {
   std::vector<uint8_t> mask;        // [ndofs] Dirichlet
   std::vector<double> metric;       // [nc][6] |det J| J^-1 J^-T (xx, xy, xz, yy, yz, zz)
   std::vector<double> absdet;       // [nc]
+  bool curved = false;              // second-order cells: metric per quadrature point
+  std::vector<double> qmetric;      // [nc][nq][6] |det J_q| J_q^-1 J_q^-T (curved)
+  std::vector<double> qdet;         // [nc][nq] |det J_q| (curved)
   // DG faces (library cell ids)
   int64_t nfi = 0, nfb = 0;
   std::vector<int32_t> fi_cell;     // [2][nfi] minus, plus
@@ -60,6 +64,9 @@ struct Ctx {
   int32_t* d_idx = nullptr;         // [ntiles][nd][kTile], constrained DoF -> -1-id
   double* d_metric64 = nullptr;     // [ntiles][6][kTile]
   float* d_metric32 = nullptr;
+  double* d_qmetric64 = nullptr;    // curved: [ntiles][nq][6][kTile]
+  float* d_qmetric32 = nullptr;
+  double* d_qdet64 = nullptr;       // curved: [ntiles][nq][kTile]
   double* d_absdet = nullptr;       // [nc]
   uint8_t* d_mask = nullptr;        // [ndofs] or null
   double* d_tab64 = nullptr;        // packed tables, see tables_layout

@@ -142,6 +142,10 @@ void colour_cells(Ctx& c) {
   permute(c.cell_dofs, nd);
   permute(c.metric, 6);
   permute(c.absdet, 1);
+  if (c.curved) {
+    permute(c.qmetric, 6 * c.nq);
+    permute(c.qdet, c.nq);
+  }
 }
 
 int build_plan(Ctx& c, const fem_mesh_desc* m) {
@@ -238,6 +242,62 @@ int build_plan(Ctx& c, const fem_mesh_desc* m) {
     out[3] = M[1][1];
     out[4] = M[1][2];
     out[5] = M[2][2];
+  }
+
+  // curved cells: Jacobian of the second-order map at every quadrature point,
+  // J[d][k] = sum_j X_j[d] d phi_j / d x_hat_k, then the same symmetric metric per point
+  if (m->cell_nodes) {
+    c.curved = true;
+    const int nq = c.tab.nq;
+    c.qmetric.assign(size_t(nc) * nq * 6, 0.0);
+    c.qdet.assign(size_t(nc) * nq, 0.0);
+    for (int64_t e = 0; e < nc; ++e) {
+      const double* X = m->cell_nodes + size_t(c.cell_perm[e]) * 30;
+      double sign = 0.0;
+      for (int q = 0; q < nq; ++q) {
+        double J[3][3];
+        for (int d = 0; d < 3; ++d)
+          for (int k = 0; k < 3; ++k) {
+            double v = 0.0;
+            for (int j = 0; j < 10; ++j) v += X[3 * j + d] * c.tab.G2[(size_t(q) * 3 + k) * 10 + j];
+            J[d][k] = v;
+          }
+        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        const double ad = std::fabs(det);
+        if (q == 0) sign = det;
+        if (!(ad > 1e-12 * std::fabs(geo[e].det)) || det * sign <= 0.0) {
+          set_error("curved cell %lld folds or degenerates at quadrature point %d", (long long)c.cell_perm[e], q);
+          return FEM_EMESH;
+        }
+        double Ji[3][3];
+        Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+        Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+        Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+        Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+        Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+        Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+        Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+        Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+        Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+        double M[3][3];
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) {
+            double sm = 0.0;
+            for (int k = 0; k < 3; ++k) sm += Ji[a][k] * Ji[b][k];
+            M[a][b] = ad * sm;
+          }
+        double* out = &c.qmetric[(size_t(e) * nq + q) * 6];
+        out[0] = M[0][0];
+        out[1] = M[0][1];
+        out[2] = M[0][2];
+        out[3] = M[1][1];
+        out[4] = M[1][2];
+        out[5] = M[2][2];
+        c.qdet[size_t(e) * nq + q] = ad;
+      }
+    }
   }
 
   // faces: sorted vertex triples, matched by sorting
@@ -540,6 +600,10 @@ int fem_create(const fem_mesh_desc* mesh, const fem_space_desc* space, fem_ctx**
   }
   if (space->dirichlet != 0 && space->dirichlet != 1) {
     set_error("fem_create: dirichlet must be 0 or 1");
+    return FEM_EINVAL;
+  }
+  if (mesh->cell_nodes && space->kind != FEM_CG) {
+    set_error("fem_create: curved cells (cell_nodes) are offered for CG spaces");
     return FEM_EINVAL;
   }
   if (space->scatter != FEM_SCATTER_ATOMIC && space->scatter != FEM_SCATTER_COLOUR) {

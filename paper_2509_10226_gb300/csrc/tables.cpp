@@ -129,6 +129,13 @@ void build_tables(int p, int s_cell, RefTables& t) {
     eval_basis(p, nodes, x, &t.V[size_t(q) * nd], &t.E[size_t(q) * 3 * nd], nd);
   }
 
+  // second-order geometry basis (curved cells) at the cell points
+  {
+    const auto nodes2 = compositions(2, 4);
+    t.G2.assign(size_t(t.nq) * 3 * 10, 0.0);
+    for (int q = 0; q < t.nq; ++q) eval_basis(2, nodes2, &t.xq[q * 3], nullptr, &t.G2[size_t(q) * 30], 10);
+  }
+
   const SimplexRule tri = gm_rule(p, 2);
   t.nqf = int(tri.w.size());
   t.wqf = tri.w;

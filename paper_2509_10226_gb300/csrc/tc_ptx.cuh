@@ -196,6 +196,11 @@ __device__ __forceinline__ void metric_pair(uint32_t* d, uint64_t M0, uint64_t M
       : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3]), "+r"(d[4]), "+r"(d[5])
       : "l"(M0), "l"(M1), "l"(M2), "l"(M3), "l"(M4), "l"(M5));
 }
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(__float_as_uint(lo)), "r"(__float_as_uint(hi)));
+  return r;
+}
 __device__ __forceinline__ uint64_t splat2(float v) {
   uint64_t r;
   asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "r"(__float_as_uint(v)));
@@ -209,9 +214,12 @@ __device__ __forceinline__ uint64_t splat2(float v) {
 // which never overtakes the columns still to be read.  kq = this cell's coefficients at the NQ
 // points, or null.  X3 (3xTF32): Q is split into a TF32 high part (kept in place) and the
 // remainder (exact in FP32, stored at column offset qlo), for the three-product GEMM 2.
-template <int ND, int NQ, bool BF16, bool HAS_K, bool X3 = false>
+// CURVED: the metric differs per point; qm points at this cell's entry (q, r) = qm[(6 q + r) * 128]
+// and a chunk's 96 values are loaded before its gradients are read from TMEM.
+template <int ND, int NQ, bool BF16, bool HAS_K, bool X3 = false, bool CURVED = false>
 __device__ __forceinline__ void metric_to_q(uint32_t lane_base, float m0, float m1, float m2, float m3, float m4,
-                                            float m5, const float* kq, uint32_t qlo = 0) {
+                                            float m5, const float* kq, uint32_t qlo = 0,
+                                            const float* __restrict__ qm = nullptr) {
   constexpr int NP = (NQ + 1) / 2;  // point pairs
   constexpr int NCHUNK = (NP + 7) / 8;
   const uint64_t M0 = splat2(m0), M1 = splat2(m1), M2 = splat2(m2), M3 = splat2(m3), M4 = splat2(m4),
@@ -220,6 +228,14 @@ __device__ __forceinline__ void metric_to_q(uint32_t lane_base, float m0, float 
   for (int c = 0; c < NCHUNK; ++c) {
     const int np = (NP - 8 * c) < 8 ? (NP - 8 * c) : 8;  // pairs in this chunk
     const int nl = (6 * np + 15) / 16;                    // x16 loads in this chunk
+    float mq[CURVED ? 96 : 1];
+    if constexpr (CURVED) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+          mq[6 * i + r] = 16 * c + i < NQ ? __ldcs(qm + (size_t(16 * c + i) * 6 + r) * kTile) : 0.0f;
+    }
     uint32_t d[48];
 #pragma unroll
     for (int l = 0; l < 3; ++l)
@@ -231,7 +247,13 @@ __device__ __forceinline__ void metric_to_q(uint32_t lane_base, float m0, float 
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       if (i < np) {
-        metric_pair(d + 6 * i, M0, M1, M2, M3, M4, M5);
+        if constexpr (CURVED) {
+          const float* a = mq + 12 * i;  // point 2i of the chunk, then point 2i + 1
+          metric_pair(d + 6 * i, pack2(a[0], a[6]), pack2(a[1], a[7]), pack2(a[2], a[8]), pack2(a[3], a[9]),
+                      pack2(a[4], a[10]), pack2(a[5], a[11]));
+        } else {
+          metric_pair(d + 6 * i, M0, M1, M2, M3, M4, M5);
+        }
         if constexpr (HAS_K) {
           const int q = 16 * c + 2 * i;
           const float k0 = kq[q], k1 = q + 1 < NQ ? kq[q + 1] : 0.0f;

@@ -37,13 +37,18 @@ class FemSpace:
     numbering.  device = -1 builds a host-only plan (queries only).  modified_rule selects the
     cell rule exact to degree 2p - 2 (Sec. 3.3; faces keep the standard rule).  scatter = "colour"
     (CG) orders the cells by colour and adds without atomics in the FP64/FP32 apply (reproducible).
+    cell_nodes [n_cells, 10, 3] makes the cells curved (second-order geometry, CG).
     """
 
     def __init__(self, xyz, cells, kind="cg", degree=1, dirichlet=False, reorder=True, penalty=None, device=0,
-                 modified_rule=False, scatter="atomic"):
+                 modified_rule=False, scatter="atomic", cell_nodes=None):
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int32)
-        mesh = _lib.MeshDesc(xyz.shape[0], xyz.ctypes.data, cells.shape[0], cells.ctypes.data)
+        nodes = None if cell_nodes is None else np.ascontiguousarray(cell_nodes, dtype=np.float64)
+        if nodes is not None and nodes.shape != (cells.shape[0], 10, 3):
+            raise ValueError("cell_nodes must be [n_cells, 10, 3]")
+        mesh = _lib.MeshDesc(xyz.shape[0], xyz.ctypes.data, cells.shape[0], cells.ctypes.data,
+                             None if nodes is None else nodes.ctypes.data)
         space = _lib.SpaceDesc(_lib.FEM_CG if kind == "cg" else _lib.FEM_DG, int(degree), int(bool(dirichlet)),
                                _lib.FEM_REORDER_MORTON if reorder else _lib.FEM_REORDER_NONE,
                                float(penalty) if penalty else 0.0, int(device),
