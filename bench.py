@@ -293,6 +293,7 @@ def main():
     ap.add_argument("--no-colour", action="store_true", help="skip the colour-scatter ablation")
     ap.add_argument("--no-smoother", action="store_true", help="skip the Chebyshev smoother sweeps")
     ap.add_argument("--no-curved", action="store_true", help="skip the curved-cell variants")
+    ap.add_argument("--no-vector", action="store_true", help="skip the vector-Laplacian variants")
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -436,6 +437,22 @@ def main():
                     del ssp, su, sy
             except Exception as e:  # noqa: BLE001
                 variants["shuffled_reorder"] = {"unavailable": str(e).splitlines()[0]}
+        if not args.no_vector:
+            # vector Laplacian, 3 components (Sec. 3.1): components-batched on the FMA units
+            try:
+                U64 = torch.stack([u64, u64.flip(0), -u64])
+                U32 = U64.float()
+                vec = {}
+                for prec, U_ in (("fp64", U64), ("fp32", U32), ("tf32", U32)):
+                    Y_ = torch.empty_like(U_)
+                    msv = time_steps(torch, lambda: sp.apply_vector(U_, prec=prec, out=Y_),
+                                     vsteps if prec != "fp64" else 3, 1, flush, stream, barrier)
+                    t = float(np.mean(msv))
+                    vec[prec] = {**tstat(msv), "gdofs": 3 * N / (t * 1e-3) / 1e9, "ms": t, "components": 3}
+                variants["vector3_p3_64"] = vec
+                del U64, U32
+            except Exception as e:  # noqa: BLE001
+                variants["vector3_p3_64"] = {"unavailable": str(e).splitlines()[0]}
         if not args.no_curved:
             # curved cells (second-order geometry, Sec. 3.2): a metric per quadrature point, 35 x 6
             # words per cell instead of 6 -- the memory-bound variant of the apply

@@ -195,6 +195,14 @@ int fem_device_status(fem_ctx* ctx, int32_t* status);
  * (EINVAL otherwise).  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
 int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k, void* stream);
 
+/* Vector Laplacian with ncomp (1..8) independent components, y_c = A u_c
+ * (the vector-valued Poisson problem of Sec. 3.1): u, y are [ncomp][N]
+ * component-major device arrays.  FEM_FP64 / FEM_FP32 run components-batched
+ * (each cell's indices, metric and tables are loaded once and serve every
+ * component); the tensor-core precisions run one pass per component.  CG
+ * only, no coefficient.  Errors as fem_apply. */
+int fem_apply_vector(fem_ctx* ctx, int32_t prec, int32_t ncomp, const void* u, void* y, void* stream);
+
 /* out = A(k)^T g (the transposed chain G^T E^T D^T E G; D_e is symmetric).
  * Same arguments and layouts as fem_apply. */
 int fem_apply_adjoint(fem_ctx* ctx, int32_t prec, const void* g, void* out, const void* k, void* stream);

@@ -121,6 +121,12 @@ def apply(xyz, cells, u, p, k=None, dirichlet_mask=None, dofs=None, modified=Fal
     return y
 
 
+def apply_vector(xyz, cells, U, p, dirichlet_mask=None, dofs=None):
+    """Vector Laplacian with independent components (the vector-valued Poisson problem of Sec. 3.1):
+    row c of the result is A applied to row c of U [ncomp, N]."""
+    return np.stack([apply(xyz, cells, U[c], p, dirichlet_mask=dirichlet_mask, dofs=dofs) for c in range(U.shape[0])])
+
+
 def apply_adjoint(xyz, cells, g, p, k=None, dirichlet_mask=None, dofs=None, modified=False):
     """A(k)^T g: the transposed chain G_e^T E^T D_e^T E G_e summed over cells."""
     if dofs is None:

@@ -66,6 +66,7 @@ _SIGNATURES = {
     "fem_dof_keys": [_P, _P],
     "fem_dof_coordinates": [_P, _P],
     "fem_colours": [_P, _P, _P],
+    "fem_apply_vector": [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P],
     "fem_chebyshev": [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _P, _P],
     "fem_lambda_max": [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P],
     "fem_smoother_work_bytes": [_P, ctypes.c_int32, _P],

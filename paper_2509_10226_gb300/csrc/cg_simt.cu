@@ -76,12 +76,14 @@ __device__ inline void gather(const int32_t* __restrict__ idx, const T* __restri
 // COLOUR: the launch covers the cells [lo, hi) of one colour (tiles from lo / 128 on), no two
 // of which share a DoF, and adds to y without atomics.
 // qmetric (curved cells, or null): [tiles][NQ][6][kT] metric per quadrature point instead of per cell.
-template <int ND, int NQ, typename T, bool COLOUR>
+// ncomp > 1: the components-batched vector Laplacian (Sec. 2.4, Sec. 3.1): ncomp independent
+// components u + c * cstride share the indices, the metric and the tables of the cell, loaded once.
+template <int ND, int NQ, typename T, bool COLOUR, bool VEC>
 __global__ void __launch_bounds__(kT) k_cg_apply(const int32_t* __restrict__ idx, const T* __restrict__ metric,
                                                  const T* __restrict__ tabE, const T* __restrict__ tabW,
                                                  const T* __restrict__ u, T* __restrict__ y,
                                                  const T* __restrict__ kcoef, int64_t nc, int64_t lo, int64_t hi,
-                                                 const T* __restrict__ qmetric) {
+                                                 const T* __restrict__ qmetric, int ncomp, int64_t cstride) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Shared<T> s = load_tables<ND, NQ, T>(smem, tabE, tabW, nullptr, false, kcoef != nullptr, false);
   const int64_t tile = (COLOUR ? lo / kT : 0) + blockIdx.x;
@@ -95,40 +97,49 @@ __global__ void __launch_bounds__(kT) k_cg_apply(const int32_t* __restrict__ idx
   int g[ND];
   T ue[ND], ye[ND];
   gather<ND, T>(idx, u, tile, lane, g, ue);
-#pragma unroll
-  for (int j = 0; j < ND; ++j) ye[j] = T(0);
   const T* mp = metric + tile * 6 * kT + lane;
   T m0 = mp[0], m1 = mp[kT], m2 = mp[2 * kT], m3 = mp[3 * kT], m4 = mp[4 * kT], m5 = mp[5 * kT];
   const T* qm = qmetric ? qmetric + tile * NQ * 6 * kT + lane : nullptr;
 
 #pragma unroll 1
-  for (int q = 0; q < NQ; ++q) {
-    if (qm) {
-      const T* p = qm + q * 6 * kT;
-      m0 = p[0], m1 = p[kT], m2 = p[2 * kT], m3 = p[3 * kT], m4 = p[4 * kT], m5 = p[5 * kT];
-    }
-    const T* Eq = s.E + q * 3 * ND;
-    T gx = T(0), gy = T(0), gz = T(0);
+  for (int comp = 0; comp < (VEC ? ncomp : 1); ++comp) {
+    T* yc = y + comp * cstride;
+    if (VEC && comp > 0) {
+      const T* uc = u + comp * cstride;
 #pragma unroll
-    for (int j = 0; j < ND; ++j) {
-      gx = fma(Eq[j], ue[j], gx);
-      gy = fma(Eq[ND + j], ue[j], gy);
-      gz = fma(Eq[2 * ND + j], ue[j], gz);
+      for (int j = 0; j < ND; ++j) ue[j] = g[j] >= 0 ? __ldg(uc + g[j]) : T(0);
     }
-    T c = s.w[q];
-    if (kcoef) c *= s.k[lane * kstride(NQ) + q];
-    const T tx = c * fma(m0, gx, fma(m1, gy, m2 * gz));
-    const T ty = c * fma(m1, gx, fma(m3, gy, m4 * gz));
-    const T tz = c * fma(m2, gx, fma(m4, gy, m5 * gz));
 #pragma unroll
-    for (int j = 0; j < ND; ++j) ye[j] = fma(Eq[j], tx, fma(Eq[ND + j], ty, fma(Eq[2 * ND + j], tz, ye[j])));
-  }
+    for (int j = 0; j < ND; ++j) ye[j] = T(0);
+#pragma unroll 1
+    for (int q = 0; q < NQ; ++q) {
+      if (qm) {
+        const T* p = qm + q * 6 * kT;
+        m0 = p[0], m1 = p[kT], m2 = p[2 * kT], m3 = p[3 * kT], m4 = p[4 * kT], m5 = p[5 * kT];
+      }
+      const T* Eq = s.E + q * 3 * ND;
+      T gx = T(0), gy = T(0), gz = T(0);
 #pragma unroll
-  for (int j = 0; j < ND; ++j)
-    if (g[j] >= 0) {
-      if constexpr (COLOUR) y[g[j]] += ye[j];
-      else atomicAdd(y + g[j], ye[j]);
+      for (int j = 0; j < ND; ++j) {
+        gx = fma(Eq[j], ue[j], gx);
+        gy = fma(Eq[ND + j], ue[j], gy);
+        gz = fma(Eq[2 * ND + j], ue[j], gz);
+      }
+      T c = s.w[q];
+      if (kcoef) c *= s.k[lane * kstride(NQ) + q];
+      const T tx = c * fma(m0, gx, fma(m1, gy, m2 * gz));
+      const T ty = c * fma(m1, gx, fma(m3, gy, m4 * gz));
+      const T tz = c * fma(m2, gx, fma(m4, gy, m5 * gz));
+#pragma unroll
+      for (int j = 0; j < ND; ++j) ye[j] = fma(Eq[j], tx, fma(Eq[ND + j], ty, fma(Eq[2 * ND + j], tz, ye[j])));
     }
+#pragma unroll
+    for (int j = 0; j < ND; ++j)
+      if (g[j] >= 0) {
+        if constexpr (COLOUR) yc[g[j]] += ye[j];
+        else atomicAdd(yc + g[j], ye[j]);
+      }
+  }  // components
 }
 
 // Backward of L = <g, A(k) u>: grad_u = A(k)^T g and dk_{e,q} = w_q gu^T M_e gg
@@ -286,29 +297,39 @@ size_t smem_bytes(bool with_k, bool with_dk) {
 }
 
 template <int ND, int NQ, typename T>
-int launch_apply(Ctx& c, const T* u, T* y, const T* k, const T* metric, const T* tab, cudaStream_t st) {
+int launch_apply(Ctx& c, const T* u, T* y, const T* k, const T* metric, const T* tab, cudaStream_t st,
+                 int ncomp = 1) {
   const T* qmetric = std::is_same<T, double>::value ? reinterpret_cast<const T*>(c.d_qmetric64)
                                                      : reinterpret_cast<const T*>(c.d_qmetric32);
   const TableLayout L = tables_layout(c.tab);
-  if (int e = init_rows<T>(y, u, c.d_mask, c.ndofs, T(0), st)) return e;
+  for (int comp = 0; comp < ncomp; ++comp)
+    if (int e = init_rows<T>(y + comp * c.ndofs, u + comp * c.ndofs, c.d_mask, c.ndofs, T(0), st)) return e;
   const size_t sm = smem_bytes<ND, NQ, T>(k != nullptr, false);
   if (c.colour_start.empty()) {
-    if (int e = allow_smem(k_cg_apply<ND, NQ, T, false>, sm)) return e;
-    k_cg_apply<ND, NQ, T, false><<<unsigned(c.ntiles), kT, sm, st>>>(c.d_idx, metric, tab + L.E, tab + L.w, u, y, k,
-                                                                    c.nc, 0, c.nc, qmetric);
+    if (ncomp > 1) {
+      if (int e = allow_smem(k_cg_apply<ND, NQ, T, false, true>, sm)) return e;
+      k_cg_apply<ND, NQ, T, false, true><<<unsigned(c.ntiles), kT, sm, st>>>(
+          c.d_idx, metric, tab + L.E, tab + L.w, u, y, k, c.nc, 0, c.nc, qmetric, ncomp, c.ndofs);
+    } else {
+      if (int e = allow_smem(k_cg_apply<ND, NQ, T, false, false>, sm)) return e;
+      k_cg_apply<ND, NQ, T, false, false><<<unsigned(c.ntiles), kT, sm, st>>>(
+          c.d_idx, metric, tab + L.E, tab + L.w, u, y, k, c.nc, 0, c.nc, qmetric, 1, c.ndofs);
+    }
     TETMF_LAUNCH_CK();
     return FEM_OK;
   }
-  // colour mode: one launch per colour, in colour order
-  if (int e = allow_smem(k_cg_apply<ND, NQ, T, true>, sm)) return e;
-  for (size_t col = 0; col + 1 < c.colour_start.size(); ++col) {
-    const int64_t lo = c.colour_start[col], hi = c.colour_start[col + 1];
-    if (hi <= lo) continue;
-    const int64_t tiles = (hi - 1) / kT - lo / kT + 1;
-    k_cg_apply<ND, NQ, T, true><<<unsigned(tiles), kT, sm, st>>>(c.d_idx, metric, tab + L.E, tab + L.w, u, y, k,
-                                                                c.nc, lo, hi, qmetric);
-    TETMF_LAUNCH_CK();
-  }
+  // colour mode: one launch per colour, in colour order (components one after the other)
+  if (int e = allow_smem(k_cg_apply<ND, NQ, T, true, false>, sm)) return e;
+  for (int comp = 0; comp < ncomp; ++comp)
+    for (size_t col = 0; col + 1 < c.colour_start.size(); ++col) {
+      const int64_t lo = c.colour_start[col], hi = c.colour_start[col + 1];
+      if (hi <= lo) continue;
+      const int64_t tiles = (hi - 1) / kT - lo / kT + 1;
+      k_cg_apply<ND, NQ, T, true, false><<<unsigned(tiles), kT, sm, st>>>(
+          c.d_idx, metric, tab + L.E, tab + L.w, u + comp * c.ndofs, y + comp * c.ndofs, k, c.nc, lo, hi, qmetric, 1,
+          c.ndofs);
+      TETMF_LAUNCH_CK();
+    }
   return FEM_OK;
 }
 
@@ -359,6 +380,17 @@ int cg_apply_simt(Ctx& c, int prec, const void* u, void* y, const void* k, bool 
   }
   TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_apply<ND, NQ, float>(c, static_cast<const float*>(u), static_cast<float*>(y),
                                                      static_cast<const float*>(k), c.d_metric32, c.d_tab32, st)))
+}
+
+int cg_apply_vector_simt(Ctx& c, int prec, int ncomp, const void* u, void* y, void* stream) {
+  cudaStream_t st = as_stream(stream);
+  if (prec == FEM_FP64) {
+    TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_apply<ND, NQ, double>(c, static_cast<const double*>(u),
+                                                                  static_cast<double*>(y), nullptr, c.d_metric64,
+                                                                  c.d_tab64, st, ncomp)))
+  }
+  TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_apply<ND, NQ, float>(c, static_cast<const float*>(u), static_cast<float*>(y),
+                                                               nullptr, c.d_metric32, c.d_tab32, st, ncomp)))
 }
 
 int cg_coeff_grad(Ctx& c, int prec, const void* u, const void* g, const void* k, void* grad_u, void* dk,

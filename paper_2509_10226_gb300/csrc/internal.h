@@ -138,6 +138,7 @@ int dg_tc_prepare(Ctx& c);
 int dg_apply_tc(Ctx& c, int prec, const void* u, void* y, void* stream);
 int dg_boundary_fp32(Ctx& c, const float* u, float* y, void* stream);  // adds the boundary-face terms
 int apply_op(Ctx& c, int prec, const void* u, void* y, void* stream);  // y = A u, no coefficient
+int cg_apply_vector_simt(Ctx& c, int prec, int ncomp, const void* u, void* y, void* stream);
 int chebyshev(Ctx& c, int prec, const void* b, void* x, const void* diag, int degree, double lam_max,
               double lam_min, void* work, void* stream);
 int lambda_max(Ctx& c, int prec, const void* diag, const void* v0, int iterations, void* work, double* lam,

@@ -804,6 +804,24 @@ int fem_smoother_work_bytes(const fem_ctx* ctx, int32_t prec, int64_t* bytes) {
   return FEM_OK;
 }
 
+int fem_apply_vector(fem_ctx* ctx, int32_t prec, int32_t ncomp, const void* u, void* y, void* stream) {
+  if (int s = check_device(ctx)) return s;
+  if (!u || !y || u == y) return set_error("fem_apply_vector: u and y must be distinct non-null"), FEM_EINVAL;
+  if (ncomp < 1 || ncomp > 8) return set_error("fem_apply_vector: ncomp must be 1..8"), FEM_EINVAL;
+  Ctx& c = ctx->c;
+  if (c.kind != FEM_CG) return set_error("fem_apply_vector: CG spaces only"), FEM_EUNSUPPORTED;
+  if (prec == FEM_FP64 || prec == FEM_FP32) return cg_apply_vector_simt(c, prec, ncomp, u, y, stream);
+  if (prec != FEM_TF32 && prec != FEM_BF16 && prec != FEM_TF32X3)
+    return set_error("fem_apply_vector: unknown precision %d", prec), FEM_EUNSUPPORTED;
+  // tensor cores: one pass per component (the 128-cell tile is the GEMM's M dimension already)
+  const size_t stride = size_t(c.ndofs) * sizeof(float);
+  for (int comp = 0; comp < ncomp; ++comp)
+    if (int s = cg_apply_tc(c, prec, static_cast<const char*>(u) + comp * stride, static_cast<char*>(y) + comp * stride,
+                            nullptr, stream))
+      return s;
+  return FEM_OK;
+}
+
 int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k, void* stream) {
   if (int s = check_device(ctx)) return s;
   if (!u || !y || u == y) return set_error("fem_apply: u and y must be distinct non-null"), FEM_EINVAL;

@@ -148,6 +148,15 @@ class FemSpace:
         call("fem_apply", self._h, PREC[prec], _ptr(u), _ptr(y), _ptr(k), _stream(stream))
         return y
 
+    def apply_vector(self, u, prec="fp64", out=None, stream=None):
+        """y[c] = A u[c] for the components c of u [ncomp, N] (vector Laplacian)."""
+        if not (isinstance(u, torch.Tensor) and u.is_cuda and u.dim() == 2 and u.shape[1] == self.n_dofs
+                and u.dtype == _vec_dtype(prec) and u.is_contiguous()):
+            raise ValueError("u must be a contiguous CUDA tensor [ncomp, n_dofs] of the precision's vector type")
+        y = torch.empty_like(u) if out is None else out
+        call("fem_apply_vector", self._h, PREC[prec], int(u.shape[0]), _ptr(u), _ptr(y), _stream(stream))
+        return y
+
     def apply_adjoint(self, g, k=None, prec="fp64", out=None, stream=None):
         self._check_vec(g, prec, "g")
         self._check_k(k, prec)
