@@ -485,7 +485,7 @@ def main():
                 sm = {}
                 for prec in ("tf32", "fp64"):
                     uu, xx = (u64, y64) if prec == "fp64" else (u32, y32)
-                    dg_ = sp.diagonal(prec=prec)
+                    dg_ = sp.diagonal(prec="fp64" if prec == "fp64" else "fp32")  # FP32 vectors for TF32
                     lam = 1.2 * sp.lambda_max(dg_, uu, iterations=20, prec=prec)
                     msv = time_steps(torch, lambda: sp.chebyshev(uu, xx, dg_, degree=5, lam_max=lam, prec=prec),
                                      vsteps if prec != "fp64" else 5, 2, flush, stream, barrier)
