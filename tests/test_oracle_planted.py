@@ -151,3 +151,17 @@ def test_wrong_chebyshev_recurrence_is_caught(monkeypatch):
     monkeypatch.setattr(smoother, "step_coefficients", wrong)
     with pytest.raises(AssertionError):
         test_error_polynomial_on_a_diagonal_operator(5)
+
+
+def test_wrong_transfer_table_is_caught(monkeypatch):
+    """Fine nodes taken in reverse order when tabulating the coarse basis breaks polynomial reproduction."""
+    import types
+
+    from oracle import transfer
+    from tests.test_oracle_transfer import test_prolongation_reproduces_coarse_polynomials
+
+    test_prolongation_reproduces_coarse_polynomials(3, 1)
+    proxy = types.SimpleNamespace(nodes_beta=lambda p: list(reversed(basis.nodes_beta(p))), values=basis.values)
+    monkeypatch.setattr(transfer, "basis", proxy)
+    with pytest.raises(AssertionError):
+        test_prolongation_reproduces_coarse_polynomials(3, 1)
