@@ -294,6 +294,7 @@ def main():
     ap.add_argument("--no-smoother", action="store_true", help="skip the Chebyshev smoother sweeps")
     ap.add_argument("--no-curved", action="store_true", help="skip the curved-cell variants")
     ap.add_argument("--no-vector", action="store_true", help="skip the vector-Laplacian variants")
+    ap.add_argument("--no-transfer", action="store_true", help="skip the p-transfer variants")
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -495,6 +496,27 @@ def main():
                 variants["chebyshev_degree5"] = sm
             except Exception as e:  # noqa: BLE001
                 variants["chebyshev_degree5"] = {"unavailable": str(e).splitlines()[0]}
+        if not args.no_transfer:
+            # p-transfer P3 -> P1 on the same mesh (the p-levels of the paper's multigrid, Sec. 4.1)
+            try:
+                from paper_2509_10226_gb300.fem import Transfer
+
+                c1 = FemSpace(xyz, cells, kind="cg", degree=1, device=local)
+                tr = Transfer(sp, c1)
+                uc = torch.as_tensor(synth.uniform_vector(c1.n_dofs, synth.SEEDS["u"]), device="cuda",
+                                     dtype=torch.float32)
+                rc = torch.empty_like(uc)
+                tv = {}
+                for name, fn in (("prolongate", lambda: tr.prolongate(uc, prec="fp32", out=y32)),
+                                 ("restrict", lambda: tr.restrict(u32, prec="fp32", out=rc))):
+                    msv = time_steps(torch, fn, vsteps, 2, flush, stream, barrier)
+                    t = float(np.mean(msv))
+                    tv[name] = {**tstat(msv), "ms": t, "fine_gdofs": N / (t * 1e-3) / 1e9}
+                variants["transfer_p3_p1_fp32"] = tv
+                tr.close()
+                del c1
+            except Exception as e:  # noqa: BLE001
+                variants["transfer_p3_p1_fp32"] = {"unavailable": str(e).splitlines()[0]}
         if not args.no_colour:
             # scatter ablation: cells ordered by colour, one launch per colour without atomics
             try:

@@ -249,6 +249,27 @@ int fem_lambda_max(fem_ctx* ctx, int32_t prec, const void* diag, const void* v0,
 /* Bytes of device scratch that fem_chebyshev and fem_lambda_max need. */
 int fem_smoother_work_bytes(const fem_ctx* ctx, int32_t prec, int64_t* bytes);
 
+/* ---- p-transfer (the p-levels of Sec. 4.1's hybrid multigrid) --------- */
+
+typedef struct fem_transfer fem_transfer;
+
+/* Transfer between two CG contexts on the same mesh (same cells, cell order,
+ * Dirichlet choice and device; build both with the same reordering and
+ * atomic scatter), fine degree above the coarse one.  Both contexts must
+ * outlive the transfer.  Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED. */
+int fem_transfer_create(fem_ctx* fine, fem_ctx* coarse, fem_transfer** out);
+int fem_transfer_destroy(fem_transfer* t);
+
+/* u_fine = P u_coarse: the coarse function evaluated at the fine nodes (exact:
+ * the coarse space is contained in the fine one); constrained fine entries
+ * are 0, constrained coarse entries of u_coarse are ignored.  Every fine
+ * entry is written.  prec FEM_FP64: double vectors, otherwise float.
+ * Asynchronous, allocates nothing. */
+int fem_prolongate(fem_transfer* t, int32_t prec, const void* u_coarse, void* u_fine, void* stream);
+
+/* r_coarse = P^T r_fine (constrained entries: 0 in, 0 out).  Asynchronous. */
+int fem_restrict(fem_transfer* t, int32_t prec, const void* r_fine, void* r_coarse, void* stream);
+
 /* ---- assembled comparator (Sec. 3.2) ------------------------------- */
 
 /* Assemble the same operator as a CSR matrix on the device (CG only;

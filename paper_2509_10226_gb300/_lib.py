@@ -66,6 +66,10 @@ _SIGNATURES = {
     "fem_dof_keys": [_P, _P],
     "fem_dof_coordinates": [_P, _P],
     "fem_colours": [_P, _P, _P],
+    "fem_transfer_create": [_P, _P, ctypes.POINTER(ctypes.c_void_p)],
+    "fem_transfer_destroy": [_P],
+    "fem_prolongate": [_P, ctypes.c_int32, _P, _P, _P],
+    "fem_restrict": [_P, ctypes.c_int32, _P, _P, _P],
     "fem_apply_vector": [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P],
     "fem_chebyshev": [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _P, _P],
     "fem_lambda_max": [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, _P],

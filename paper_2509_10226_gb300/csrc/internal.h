@@ -144,6 +144,13 @@ int chebyshev(Ctx& c, int prec, const void* b, void* x, const void* diag, int de
 int lambda_max(Ctx& c, int prec, const void* diag, const void* v0, int iterations, void* work, double* lam,
                void* stream);
 size_t lambda_max_work_bytes(const Ctx& c, int prec);  // also enough for chebyshev
+// p-transfer (transfer.cu)
+struct Transfer;
+int transfer_create(Ctx& fine, Ctx& coarse, Transfer** out);
+void transfer_destroy(Transfer* t);
+int transfer_apply(Transfer& t, int prec, bool prolong, const void* in, void* out, void* stream);
+// tab[i][j] = phi_j of degree p_coarse at the reference node i of degree p_fine (beta order)
+void fine_nodes_coarse_values(int p_fine, int p_coarse, std::vector<double>& tab);
 
 }  // namespace tetmf
 

@@ -570,6 +570,10 @@ int apply_op(Ctx& c, int prec, const void* u, void* y, void* stream) {
 
 using namespace tetmf;
 
+struct fem_transfer {
+  tetmf::Transfer* t = nullptr;
+};
+
 extern "C" {
 
 const char* fem_last_error(void) { return g_err; }
@@ -802,6 +806,39 @@ int fem_smoother_work_bytes(const fem_ctx* ctx, int32_t prec, int64_t* bytes) {
   if (!bytes) return set_error("null output"), FEM_EINVAL;
   *bytes = int64_t(lambda_max_work_bytes(ctx->c, prec));
   return FEM_OK;
+}
+
+int fem_transfer_create(fem_ctx* fine, fem_ctx* coarse, fem_transfer** out) {
+  if (int s = check_device(fine)) return s;
+  if (int s = check_device(coarse)) return s;
+  if (!out) return set_error("fem_transfer_create: null output"), FEM_EINVAL;
+  fem_transfer* h = new (std::nothrow) fem_transfer;
+  if (!h) return set_error("fem_transfer_create: out of host memory"), FEM_ENOMEM;
+  if (int s = transfer_create(fine->c, coarse->c, &h->t)) {
+    delete h;
+    return s;
+  }
+  *out = h;
+  return FEM_OK;
+}
+
+int fem_transfer_destroy(fem_transfer* t) {
+  if (!t) return FEM_OK;
+  transfer_destroy(t->t);
+  delete t;
+  return FEM_OK;
+}
+
+int fem_prolongate(fem_transfer* t, int32_t prec, const void* u_coarse, void* u_fine, void* stream) {
+  if (!t || !u_coarse || !u_fine) return set_error("fem_prolongate: null pointer"), FEM_EINVAL;
+  if (prec < FEM_FP64 || prec > FEM_TF32X3) return set_error("fem_prolongate: unknown precision %d", prec), FEM_EINVAL;
+  return transfer_apply(*t->t, prec, true, u_coarse, u_fine, stream);
+}
+
+int fem_restrict(fem_transfer* t, int32_t prec, const void* r_fine, void* r_coarse, void* stream) {
+  if (!t || !r_fine || !r_coarse) return set_error("fem_restrict: null pointer"), FEM_EINVAL;
+  if (prec < FEM_FP64 || prec > FEM_TF32X3) return set_error("fem_restrict: unknown precision %d", prec), FEM_EINVAL;
+  return transfer_apply(*t->t, prec, false, r_fine, r_coarse, stream);
 }
 
 int fem_apply_vector(fem_ctx* ctx, int32_t prec, int32_t ncomp, const void* u, void* y, void* stream) {

@@ -163,6 +163,16 @@ void build_tables(int p, int s_cell, RefTables& t) {
     }
 }
 
+void fine_nodes_coarse_values(int p_fine, int p_coarse, std::vector<double>& tab) {
+  const auto fine = compositions(p_fine, 4), coarse = compositions(p_coarse, 4);
+  const int ndf = int(fine.size()), ndc = int(coarse.size());
+  tab.assign(size_t(ndf) * ndc, 0.0);
+  for (int i = 0; i < ndf; ++i) {
+    const double x[3] = {double(fine[i][1]) / p_fine, double(fine[i][2]) / p_fine, double(fine[i][3]) / p_fine};
+    eval_basis(p_coarse, coarse, x, &tab[size_t(i) * ndc], nullptr, ndc);
+  }
+}
+
 TableLayout tables_layout(const RefTables& t) {
   TableLayout L;
   int64_t off = 0;

@@ -243,6 +243,38 @@ class FemSpace:
         return x, stats
 
 
+class Transfer:
+    """Prolongation / restriction between two CG spaces of different degree on one mesh."""
+
+    def __init__(self, fine: FemSpace, coarse: FemSpace):
+        h = ctypes.c_void_p()
+        call("fem_transfer_create", fine._h, coarse._h, ctypes.byref(h))
+        self._h, self.fine, self.coarse = h, fine, coarse  # the spaces must outlive the transfer
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().fem_transfer_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def prolongate(self, uc, prec="fp64", out=None, stream=None):
+        self.coarse._check_vec(uc, prec, "u_coarse")
+        uf = torch.empty(self.fine.n_dofs, dtype=uc.dtype, device=uc.device) if out is None else out
+        call("fem_prolongate", self._h, PREC[prec], _ptr(uc), _ptr(uf), _stream(stream))
+        return uf
+
+    def restrict(self, rf, prec="fp64", out=None, stream=None):
+        self.fine._check_vec(rf, prec, "r_fine")
+        rc = torch.empty(self.coarse.n_dofs, dtype=rf.dtype, device=rf.device) if out is None else out
+        call("fem_restrict", self._h, PREC[prec], _ptr(rf), _ptr(rc), _stream(stream))
+        return rc
+
+
 class FemApply(torch.autograd.Function):
     """y = A(k) u with a hand-written backward (fem_coeff_grad):
     dL/du = A(k)^T (dL/dy) and dL/dk_{e,q} = w_q |det J_e| (grad u . grad dL/dy)."""
