@@ -97,6 +97,12 @@ extern "C" {
 #define FEM_SOLVE_FP64_PCG 0   /* Jacobi-PCG, FP64 operator and vectors      */
 #define FEM_SOLVE_IR_MIXED 1   /* FP64 iterative refinement around an inner  */
                                /* FP32-vector Jacobi-PCG (inner_prec apply)  */
+#define FEM_SOLVE_IR_PMG 2     /* the same refinement around an inner flexible */
+                               /* CG preconditioned by a two-level p-multigrid */
+                               /* V-cycle (Chebyshev-Jacobi smoothing on the   */
+                               /* space, fixed-step Jacobi-PCG on linear       */
+                               /* elements of the same mesh; degree >= 2,      */
+                               /* straight cells, atomic scatter)              */
 
 typedef struct fem_ctx fem_ctx;
 
@@ -281,12 +287,14 @@ int fem_csr_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, void* stre
 
 /* ---- solve (blocking) ---------------------------------------------- */
 typedef struct {
-  int32_t mode;          /* FEM_SOLVE_FP64_PCG or FEM_SOLVE_IR_MIXED         */
+  int32_t mode;          /* FEM_SOLVE_FP64_PCG, _IR_MIXED or _IR_PMG         */
   int32_t inner_prec;    /* IR: FEM_FP32, FEM_TF32, FEM_BF16 or FEM_TF32X3    */
   double rtol;           /* stop when ||b - A x|| / ||b|| <= rtol (FP64)     */
   double inner_rtol;     /* IR: relative reduction asked of each inner solve */
   int32_t max_outer;     /* IR outer iterations cap                          */
   int32_t max_inner;     /* PCG iterations cap (per inner solve for IR)      */
+  int32_t smoother_degree; /* IR_PMG: Chebyshev steps per smoothing (0: 5)   */
+  int32_t coarse_steps;  /* IR_PMG: coarse Jacobi-PCG steps (0: 20)          */
 } fem_solve_opts;
 
 typedef struct {

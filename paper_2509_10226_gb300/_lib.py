@@ -19,7 +19,7 @@ FEM_RULE_STANDARD, FEM_RULE_MODIFIED = 0, 1
 FEM_SCATTER_ATOMIC, FEM_SCATTER_COLOUR = 0, 1
 FEM_FP64, FEM_FP32, FEM_TF32, FEM_BF16, FEM_TF32X3 = 0, 1, 2, 3, 4
 FEM_REORDER_NONE, FEM_REORDER_MORTON = 0, 1
-FEM_SOLVE_FP64_PCG, FEM_SOLVE_IR_MIXED = 0, 1
+FEM_SOLVE_FP64_PCG, FEM_SOLVE_IR_MIXED, FEM_SOLVE_IR_PMG = 0, 1, 2
 
 STATUS_NAMES = {0: "FEM_OK", 1: "FEM_EINVAL", 2: "FEM_EMESH", 3: "FEM_EUNSUPPORTED", 4: "FEM_ECUDA",
                 5: "FEM_ENOTCONV", 6: "FEM_ENOMEM"}
@@ -44,7 +44,8 @@ class SpaceDesc(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("inner_prec", ctypes.c_int32), ("rtol", ctypes.c_double),
-                ("inner_rtol", ctypes.c_double), ("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32)]
+                ("inner_rtol", ctypes.c_double), ("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32),
+                ("smoother_degree", ctypes.c_int32), ("coarse_steps", ctypes.c_int32)]
 
 
 class SolveStats(ctypes.Structure):

@@ -108,6 +108,7 @@ struct Ctx {
   void* d_work = nullptr;
   size_t work_bytes = 0;
 
+  void* pmg = nullptr;               // p-multigrid hierarchy of the solver (pmg.cu), built on first use
   std::vector<void*> allocations;   // every cudaMalloc, freed by destroy
 };
 
@@ -144,6 +145,11 @@ int chebyshev(Ctx& c, int prec, const void* b, void* x, const void* diag, int de
 int lambda_max(Ctx& c, int prec, const void* diag, const void* v0, int iterations, void* work, double* lam,
                void* stream);
 size_t lambda_max_work_bytes(const Ctx& c, int prec);  // also enough for chebyshev
+// p-multigrid (pmg.cu)
+int pmg_setup(Ctx& c, int prec, const float* diag, int degree, int coarse_steps, void* stream);
+int pmg_inner_solve(Ctx& c, const float* diag, float* r, float* d, float* p, float* q, double rtol, int max_it,
+                    int& iters, void* stream);
+void pmg_release(Ctx& c);
 // p-transfer (transfer.cu)
 struct Transfer;
 int transfer_create(Ctx& fine, Ctx& coarse, Transfer** out);

@@ -950,9 +950,9 @@ int fem_solve(fem_ctx* ctx, const fem_solve_opts* opts, const double* b, double*
   if (!opts || !b || !x || !stats || (const void*)b == (const void*)x)
     return set_error("fem_solve: null or aliased argument"), FEM_EINVAL;
   if (ctx->c.kind != FEM_CG) return set_error("fem_solve: CG spaces only"), FEM_EINVAL;
-  if (opts->mode != FEM_SOLVE_FP64_PCG && opts->mode != FEM_SOLVE_IR_MIXED)
+  if (opts->mode != FEM_SOLVE_FP64_PCG && opts->mode != FEM_SOLVE_IR_MIXED && opts->mode != FEM_SOLVE_IR_PMG)
     return set_error("fem_solve: bad mode"), FEM_EINVAL;
-  if (opts->mode == FEM_SOLVE_IR_MIXED && opts->inner_prec != FEM_FP32 && opts->inner_prec != FEM_TF32 &&
+  if (opts->mode != FEM_SOLVE_FP64_PCG && opts->inner_prec != FEM_FP32 && opts->inner_prec != FEM_TF32 &&
       opts->inner_prec != FEM_BF16 && opts->inner_prec != FEM_TF32X3)
     return set_error("fem_solve: inner_prec must be FEM_FP32, FEM_TF32, FEM_BF16 or FEM_TF32X3"), FEM_EUNSUPPORTED;
   if (!(opts->rtol > 0) || opts->max_inner < 1 || opts->max_outer < 1)

@@ -10,6 +10,9 @@
 //                      tensor-core apply, FP64 dot products) to inner_rtol
 //                      x += ||r|| d                FP64 update
 //
+// FEM_SOLVE_IR_PMG replaces the inner Jacobi-PCG by flexible CG preconditioned by a p-multigrid
+// V-cycle (pmg.cu).
+//
 // Every reduction is a single kernel: each block writes a partial sum to a
 // scratch array, and the last block to finish (atomic ticket) adds the
 // partials in block order, so results are deterministic.  Scalars (alpha,
@@ -18,13 +21,12 @@
 #include <cmath>
 #include <mutex>
 
+#include "blas.cuh"
 #include "common.cuh"
 
 namespace tetmf {
 namespace {
 
-constexpr int kBlock = 256;
-constexpr int kMaxRedBlocks = 1024;
 constexpr int kCheck = 8;  // PCG iterations between residual checks on the host
 
 // scalar slots in the solver's device scalar array
@@ -48,73 +50,9 @@ struct Work {
   double* host_scal;     // pinned host mirror
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
-// block-reduce two values; the last block adds all partials and stores them
-__device__ void finish2(double v0, double v1, double* partials, unsigned* ticket, double* out0, double* out1) {
-  __shared__ double s0[kBlock / 32], s1[kBlock / 32];
-  __shared__ bool last;
-  v0 = warp_sum(v0);
-  v1 = warp_sum(v1);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) {
-    s0[w] = v0;
-    s1[w] = v1;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < kBlock / 32; ++i) {
-      a += s0[i];
-      b += s1[i];
-    }
-    partials[2 * blockIdx.x] = a;
-    partials[2 * blockIdx.x + 1] = b;
-    __threadfence();
-    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < int(gridDim.x); i += kBlock) {
-    a += partials[2 * i];
-    b += partials[2 * i + 1];
-  }
-  a = warp_sum(a);
-  b = warp_sum(b);
-  if (l == 0) {
-    s0[w] = a;
-    s1[w] = b;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double x = 0.0, y = 0.0;
-    for (int i = 0; i < kBlock / 32; ++i) {
-      x += s0[i];
-      y += s1[i];
-    }
-    if (out0) *out0 = x;
-    if (out1) *out1 = y;
-    *ticket = 0u;
-  }
-}
 
-#define GRID_STRIDE(i, n) \
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < (n); i += int64_t(gridDim.x) * blockDim.x)
 
-// out0 = a . b
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_dot(const T* __restrict__ a, const T* __restrict__ b, int64_t n,
-                                                double* partials, unsigned* ticket, double* out0) {
-  double s = 0.0;
-  GRID_STRIDE(i, n) s = fma(double(a[i]), double(b[i]), s);
-  finish2(s, 0.0, partials, ticket, out0, nullptr);
-}
 
 // r = b - Ax (FP64), scal[S_RR] = r . r
 __global__ void __launch_bounds__(kBlock) k_residual64(const double* __restrict__ b, const double* __restrict__ ax,
@@ -146,70 +84,11 @@ __global__ void k_correct(double* __restrict__ x, const float* __restrict__ d, c
   GRID_STRIDE(i, n) x[i] = fma(s, double(d[i]), x[i]);
 }
 
-// PCG start: z = r / diag, p = z, rz = r . z, rr = r . r
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_pcg_start(const T* __restrict__ r, const T* __restrict__ diag,
-                                                      T* __restrict__ z, T* __restrict__ p, int64_t n,
-                                                      double* partials, unsigned* ticket, double* rz, double* rr) {
-  double a = 0.0, b = 0.0;
-  GRID_STRIDE(i, n) {
-    const T ri = r[i];
-    const T zi = ri / diag[i];
-    z[i] = zi;
-    p[i] = zi;
-    a = fma(double(ri), double(zi), a);
-    b = fma(double(ri), double(ri), b);
-  }
-  finish2(a, b, partials, ticket, rz, rr);
-}
 
-// alpha = rz / pq; x += alpha p; r -= alpha q; z = r / diag; rz' = r . z; rr = r . r
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_pcg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
-                                                       const T* __restrict__ p, const T* __restrict__ q,
-                                                       const T* __restrict__ diag, int64_t n, const double* rz,
-                                                       const double* pq, double* partials, unsigned* ticket,
-                                                       double* rz_next, double* rr) {
-  const double pqv = *pq;
-  const T alpha = pqv != 0.0 ? T(*rz / pqv) : T(0);
-  double a = 0.0, b = 0.0;
-  GRID_STRIDE(i, n) {
-    x[i] = fma(alpha, p[i], x[i]);
-    const T ri = fma(-alpha, q[i], r[i]);
-    r[i] = ri;
-    const T zi = ri / diag[i];
-    z[i] = zi;
-    a = fma(double(ri), double(zi), a);
-    b = fma(double(ri), double(ri), b);
-  }
-  finish2(a, b, partials, ticket, rz_next, rr);
-}
 
-// beta = rz' / rz; p = z + beta p
-template <typename T>
-__global__ void k_pcg_direction(T* __restrict__ p, const T* __restrict__ z, int64_t n, const double* rz_next,
-                                const double* rz) {
-  const double rzv = *rz;
-  const T beta = rzv != 0.0 ? T(*rz_next / rzv) : T(0);
-  GRID_STRIDE(i, n) p[i] = fma(beta, p[i], z[i]);
-}
 
-template <typename T>
-__global__ void k_cast(const double* __restrict__ a, T* __restrict__ b, int64_t n) {
-  GRID_STRIDE(i, n) b[i] = T(a[i]);
-}
 
-int red_grid(int64_t n) {
-  int64_t g = (n + kBlock - 1) / kBlock;
-  const int64_t cap = std::min<int64_t>(kMaxRedBlocks, int64_t(sm_count()) * 4);
-  return int(g < 1 ? 1 : (g > cap ? cap : g));
-}
 
-int ew_grid(int64_t n) {
-  int64_t g = (n + kBlock - 1) / kBlock;
-  const int64_t cap = int64_t(sm_count()) * 8;
-  return int(g < 1 ? 1 : (g > cap ? cap : g));
-}
 
 // lay the solver's work arrays out from `base` (nullptr: only measure); returns the bytes used
 size_t carve(uint8_t* base, int64_t N, Work& w) {
@@ -367,6 +246,9 @@ static int solve_with(Ctx& c, Work& w, const fem_solve_opts* o, const double* b,
                           : cg_apply_tc(c, ip, in, out, nullptr, stream);
   };
   const double inner = o->inner_rtol > 0 ? o->inner_rtol : 1e-3;
+  const bool pmg = o->mode == FEM_SOLVE_IR_PMG;
+  if (pmg)
+    if (int e = pmg_setup(c, ip, w.diag32, o->smoother_degree, o->coarse_steps, stream)) return e;
   for (;;) {
     if (int e = residual(rel)) return e;
     if (rel <= o->rtol) return finish(FEM_OK, rel);
@@ -375,7 +257,9 @@ static int solve_with(Ctx& c, Work& w, const fem_solve_opts* o, const double* b,
     k_scale_down<<<eg, kBlock, 0, st>>>(w.r64, w.scal + S_RES, r32, d32, N);
     TETMF_LAUNCH_CK();
     int it = 0;
-    const int e = pcg<float>(c, w, apply32, d32, r32, z32, p32, q32, w.diag32, inner * inner, o->max_inner, it, st);
+    const int e = pmg ? pmg_inner_solve(c, w.diag32, r32, d32, p32, q32, inner, o->max_inner, it, stream)
+                      : pcg<float>(c, w, apply32, d32, r32, z32, p32, q32, w.diag32, inner * inner, o->max_inner, it,
+                                   st);
     stats->inner_iterations += it;
     stats->outer_iterations += 1;
     if (e && e != FEM_ENOTCONV) return e;
@@ -457,6 +341,10 @@ extern "C" int fem_solve_noalloc(fem_ctx* ctx, const fem_solve_opts* opts, const
   if (c.kind != FEM_CG) {
     set_error("fem_solve_noalloc: CG spaces only");
     return FEM_EINVAL;
+  }
+  if (opts->mode == FEM_SOLVE_IR_PMG) {
+    set_error("fem_solve_noalloc: the p-multigrid hierarchy is allocated; use fem_solve");
+    return FEM_EUNSUPPORTED;
   }
   if (opts->mode != FEM_SOLVE_FP64_PCG && opts->mode != FEM_SOLVE_IR_MIXED) {
     set_error("fem_solve_noalloc: bad mode");

@@ -222,8 +222,11 @@ class FemSpace:
         return lam.value
 
     def solve(self, b, x0=None, mode="ir", inner_prec="fp32", rtol=1e-10, inner_rtol=1e-3, max_outer=50,
-              max_inner=20000, stream=None, raise_on_notconv=True, no_alloc=False):
-        """Solve A x = b (blocking).  Returns (x, stats dict).
+              max_inner=20000, stream=None, raise_on_notconv=True, no_alloc=False, smoother_degree=0,
+              coarse_steps=0):
+        """Solve A x = b (blocking).  Returns (x, stats dict).  mode: "pcg" (FP64 Jacobi-PCG), "ir"
+        (FP64 refinement around FP32-vector Jacobi-PCG), "pmg" (the same refinement around flexible
+        CG with a p-multigrid V-cycle).
 
         no_alloc=True calls fem_solve_noalloc: the same solver with its work space in
         the library's fixed device array instead of memory the context allocates (for
@@ -231,8 +234,9 @@ class FemSpace:
         FEM_SOLVE_NOALLOC_MAX_DOFS unknowns, concurrent calls must be serialised)."""
         self._check_vec(b, "fp64", "b")
         x = torch.zeros_like(b) if x0 is None else x0.clone()
-        opts = _lib.SolveOpts(_lib.FEM_SOLVE_IR_MIXED if mode == "ir" else _lib.FEM_SOLVE_FP64_PCG, PREC[inner_prec],
-                              rtol, inner_rtol, max_outer, max_inner)
+        modes = {"ir": _lib.FEM_SOLVE_IR_MIXED, "pcg": _lib.FEM_SOLVE_FP64_PCG, "pmg": _lib.FEM_SOLVE_IR_PMG}
+        opts = _lib.SolveOpts(modes[mode], PREC[inner_prec], rtol, inner_rtol, max_outer, max_inner,
+                              int(smoother_degree), int(coarse_steps))
         st = _lib.SolveStats()
         fn = _lib.lib().fem_solve_noalloc if no_alloc else _lib.lib().fem_solve
         status = fn(self._h, ctypes.byref(opts), _ptr(b), _ptr(x), ctypes.byref(st), _stream(stream))

@@ -122,3 +122,32 @@ def test_config5_cg_p3_48cubed_mixed():
     assert np.allclose(bh[sample], b_ref, rtol=0, atol=1e-13 * np.abs(bh).max())
     ax = sampled_rows(sp, xyz, cells, p, to_host(x_ir), sample, mask_lib=mask)
     assert np.abs(b_ref - ax).max() <= 1e-9 * np.abs(bh).max()
+
+
+@pytest.mark.parametrize("p,inner", [(2, "tf32"), (3, "tf32"), (3, "fp32"), (3, "bf16")])
+def test_pmg_solve(p, inner):
+    """Refinement around flexible CG with the p-multigrid V-cycle: converges to 1e-10 (the oracle's
+    residual agrees) in far fewer inner iterations than Jacobi-PCG."""
+    sp, xyz, cells, dofs, keys, mask = setup_problem(6, p)
+    perm = sp.dof_permutation()
+    b = sp.rhs_const(1.0)
+    x, st = sp.solve(b, mode="pmg", inner_prec=inner, rtol=1e-10, inner_rtol=1e-3)
+    assert st["converged"] and st["rel_residual"] <= 1e-10
+    b_can = np.empty(sp.n_dofs)
+    b_can[perm] = to_host(b)
+    x_can = np.empty(sp.n_dofs)
+    x_can[perm] = to_host(x)
+    assert oracle_residual(xyz, cells, p, dofs, mask, x_can, b_can) <= 1e-10
+    _, st_j = sp.solve(b, mode="ir", inner_prec=inner, rtol=1e-10, inner_rtol=1e-3)
+    assert st["inner"] < st_j["inner"] / 2, (st["inner"], st_j["inner"])
+
+
+def test_pmg_refusals():
+    from paper_2509_10226_gb300 import FemError
+
+    sp, xyz, cells, dofs, keys, mask = setup_problem(3, 1)
+    with pytest.raises(FemError, match="degree >= 2"):
+        sp.solve(sp.rhs_const(1.0), mode="pmg", inner_prec="tf32")
+    sp2, *_ = setup_problem(3, 2)
+    with pytest.raises(FemError, match="allocated"):
+        sp2.solve(sp2.rhs_const(1.0), mode="pmg", inner_prec="tf32", no_alloc=True)
