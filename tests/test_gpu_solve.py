@@ -107,13 +107,15 @@ def test_config5_cg_p3_48cubed_mixed():
     assert int(sp.dirichlet_mask().sum()) == 3048625 - 143 ** 3
     b = sp.rhs_const(1.0)
     x_ir, st_ir = sp.solve(b, mode="ir", inner_prec="tf32", rtol=1e-10, inner_rtol=1e-3)
+    x_mg, st_mg = sp.solve(b, mode="pmg", inner_prec="tf32", rtol=1e-10, inner_rtol=1e-5)
     x_64, st_64 = sp.solve(b, mode="pcg", rtol=1e-10)
-    assert st_ir["converged"] and st_64["converged"]
-    for x in (x_ir, x_64):
+    assert st_ir["converged"] and st_mg["converged"] and st_64["converged"]
+    for x in (x_ir, x_mg, x_64):
         r = b - sp.apply(x)
         assert float(torch.linalg.norm(r) / torch.linalg.norm(b)) <= 1e-10
-    # both solutions agree within the conditioning of the problem
-    assert float(torch.linalg.norm(x_ir - x_64) / torch.linalg.norm(x_64)) <= 1e-6
+    # the solutions agree within the conditioning of the problem
+    for x in (x_ir, x_mg):
+        assert float(torch.linalg.norm(x - x_64) / torch.linalg.norm(x_64)) <= 1e-6
     # oracle on 256 sampled rows: b and (A x) agree to 1e-10 ||b||_inf
     mask = sp.dirichlet_mask()
     sample = np.random.default_rng(14).choice(sp.n_dofs, 256, replace=False)
