@@ -27,7 +27,7 @@ def _gpu():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_config1_cg_p2_8cubed(prec):
+def test_cg_p2_8cubed(prec):
     """CG P2 on the 8^3 Kuhn cube (3072 cells, 24 tiles), jitter 0.2h, u ~ U[-1,1]."""
     sp, xyz, cells, dofs, keys = make(8, 2)
     assert sp.n_dofs == 4913
@@ -35,7 +35,7 @@ def test_config1_cg_p2_8cubed(prec):
     u = synth.uniform_vector(sp.n_dofs, synth.SEEDS["u"])
     y_ref = cg.apply(xyz, cells, u, 2, dofs=dofs)
     y = to_host(sp.apply(to_dev(u[perm], prec), prec=prec))
-    assert_close(y, y_ref[perm], prec, "config1")
+    assert_close(y, y_ref[perm], prec, "CG P2 8^3")
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
@@ -67,7 +67,7 @@ def test_single_cell():
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_variable_coefficient_adjoint_and_gradient(prec):
-    """Config-4 structure on 6^3 (1296 cells): k ~ lognormal(0, 0.5) per quadrature point."""
+    """Variable coefficient on 6^3 (1296 cells): k ~ lognormal(0, 0.5) per quadrature point."""
     p = 2
     sp, xyz, cells, dofs, keys = make(6, p, seed=3)
     perm, cperm = sp.dof_permutation(), sp.cell_permutation()
@@ -132,7 +132,7 @@ def test_autograd_function():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16", "tf32x3"])
-def test_config2_full_size_sampled(prec):
+def test_cg_p3_64cubed_full_size_sampled(prec):
     """CG P3 on the 64^3 Kuhn cube (1,572,864 cells, 7,189,057 DoFs), Morton order, the launch the
     benchmark times: 512 sampled rows against the oracle, plus A 1 = 0 and u^T A u = |a|^2."""
     from paper_2509_10226_gb300.fem import FemSpace
@@ -147,7 +147,7 @@ def test_config2_full_size_sampled(prec):
     sample = rng.choice(sp.n_dofs, 512, replace=False)
     y_ref = sampled_rows(sp, xyz, cells, p, u, sample)
     # the sample's scale: rows of A u are O(h) sums with cancellation; compare against the sampled max
-    assert_close(y[sample], y_ref, prec, "config2 sampled")
+    assert_close(y[sample], y_ref, prec, "CG P3 64^3 sampled")
     # properties that hold at any size
     ones = to_host(sp.apply(to_dev(np.ones(sp.n_dofs), prec), prec=prec))
     term = np.abs(y).max()
@@ -179,15 +179,15 @@ def test_tensor_core_degrees_ragged(p, prec):
 
 
 @pytest.mark.parametrize("prec", ["tf32", "bf16", "tf32x3"])
-def test_tensor_core_config1_variable_k_dirichlet(prec):
-    """Config-1 mesh (8^3, 24 tiles) on the tensor cores: plain, with k ~ lognormal(0, 0.5), and with
+def test_tensor_core_p2_8cubed_variable_k_dirichlet(prec):
+    """The 8^3 mesh (3072 cells, 24 tiles) on the tensor cores: plain, with k ~ lognormal(0, 0.5), and with
     Dirichlet rows; several tiles per persistent CTA are exercised on the 64^3 test below."""
     p = 2
     sp, xyz, cells, dofs, keys = make(8, p)
     perm, cperm = sp.dof_permutation(), sp.cell_permutation()
     u = synth.uniform_vector(sp.n_dofs, 1)
     y = to_host(sp.apply(to_dev(u[perm], prec), prec=prec))
-    assert_close(y, cg.apply(xyz, cells, u, p, dofs=dofs)[perm], prec, "config1")
+    assert_close(y, cg.apply(xyz, cells, u, p, dofs=dofs)[perm], prec, "CG P2 8^3")
     k_user = synth.lognormal_coefficients((cells.shape[0], sp.n_qpoints), 3)
     y = to_host(sp.apply(to_dev(u[perm], prec), k=to_dev(k_user[cperm].ravel(), prec), prec=prec))
     assert_close(y, cg.apply(xyz, cells, u, p, k=k_user, dofs=dofs)[perm], prec, "variable k")
@@ -200,8 +200,8 @@ def test_tensor_core_config1_variable_k_dirichlet(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_config4_p2_32cubed_variable_k_backward(prec):
-    """Config 4: CG P2 on the 32^3 cube (196,608 cells), k ~ lognormal(0, 0.5) per quadrature point,
+def test_cg_p2_32cubed_variable_k_backward(prec):
+    """CG P2 on the 32^3 cube (196,608 cells), k ~ lognormal(0, 0.5) per quadrature point,
     L = <w, A(k) u>: forward rows, grad_u = A(k)^T w rows and dL/dk on sampled cells against the
     oracle; central differences of L in k through the GPU forward."""
     from oracle import cg as ocg

@@ -43,7 +43,7 @@ def test_csr_matches_oracle(p, dirichlet):
         assert nnz == len(pairs)
 
 
-def test_csr_config2_full_size():
+def test_csr_cg_p3_64cubed_full_size():
     """P3 64^3 (314M stored entries): 512 sampled rows of the CSR SpMV against the oracle."""
     from paper_2509_10226_gb300.fem import FemSpace
 
@@ -57,4 +57,4 @@ def test_csr_config2_full_size():
     y_ref = sampled_rows(sp, xyz, cells, p, u, sample)
     for prec in ("fp64", "fp32"):
         y = to_host(sp.csr_apply(to_dev(u, prec), prec=prec))
-        assert_close(y[sample], y_ref, prec, "csr config2 sampled")
+        assert_close(y[sample], y_ref, prec, "csr CG P3 64^3 sampled")

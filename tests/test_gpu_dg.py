@@ -53,7 +53,7 @@ def test_dg_custom_penalty_and_adjoint():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
-def test_config3_dg_p2_48cubed_sampled(prec):
+def test_dg_p2_48cubed_sampled(prec):
     """DG SIPG P2 on the 48^3 Kuhn cube (663,552 cells, 1,313,280 interior + 27,648 boundary faces):
     256 sampled cells against the oracle evaluated on the sampled cells and their face neighbours."""
     from paper_2509_10226_gb300.fem import FemSpace
@@ -76,7 +76,7 @@ def test_config3_dg_p2_48cubed_sampled(prec):
     u_sub = u_user.reshape(-1, nd)[sub].ravel()
     y_sub = dg.apply(xyz, cells[sub], u_sub, p).reshape(-1, nd)
     y_ref = y_sub[np.searchsorted(sub, sample)]
-    assert_close(y_user.reshape(-1, nd)[sample], y_ref, prec, "config3 sampled")
+    assert_close(y_user.reshape(-1, nd)[sample], y_ref, prec, "DG P2 48^3 sampled")
 
 
 @pytest.mark.parametrize("prec", ["tf32", "bf16"])

@@ -93,8 +93,8 @@ def test_zero_rhs_and_initial_guess():
     assert st2["inner"] <= 1
 
 
-def test_config5_cg_p3_48cubed_mixed():
-    """Config 5: CG P3 on the 48^3 cube (663,552 cells, 3,048,625 DoFs, Dirichlet), f = 1, IR with the
+def test_solve_cg_p3_48cubed_mixed():
+    """CG P3 on the 48^3 cube (663,552 cells, 3,048,625 DoFs, Dirichlet), f = 1, IR with the
     TF32 tensor-core inner PCG and FP64 outer residual to 1e-10, against the all-FP64 PCG; the final
     residual is recomputed with the FP64 library operator (pinned to the oracle above) and on 256
     rows by the oracle."""
