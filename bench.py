@@ -362,7 +362,7 @@ def main():
     traffic = profiled_traffic(["cg_tc.cu", "tc_ptx.cuh"], "k_cg_apply_tc.cg_p3_64.md") if n == 64 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "algorithmic_bytes": hb,
-                "kernel": "fem_apply tf32 (zero-fill + k_cg_apply_tc)",
+                "kernel": "fem_apply tf32 (zero-fill + k_cg_apply_tc_ws)",
                 "peak_source": peaks["source"] + " hbm_gbs (burst copy)"}
 
     # end to end: pinned host u -> device, apply, device -> host y, every step

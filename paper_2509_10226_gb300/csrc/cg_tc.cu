@@ -35,6 +35,9 @@
 //      tile's rows are built;
 //   5. each thread reads its row of Y', pre-reduces it into shared memory,
 //      and the warpgroup adds the tile's distinct values to y with atomics.
+// Where TMEM admits at most three tiles per SM (P3, P4) and there is no coefficient, the
+// warp-specialised kernel below takes step 5 off the compute warpgroups: a fourth warpgroup
+// scatters every finished tile while they carry on with the next.
 // Every wait on an MMA completion is bounded (about 1 s); on time-out the
 // kernel records bit 0 in the status word and stops after freeing its TMEM.
 //
@@ -424,6 +427,266 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3, CURVED>()
   if (failed && m == 0) atomicOr(status, 1);
 }
 
+// ---- warp-specialised variant ----------------------------------------------------------------
+// G compute warpgroups (one TMEM tile each: rows, GEMM 1, metric step, GEMM 2) and one scatter
+// warpgroup that takes every finished tile off their hands: it reads Y' straight from the compute
+// warpgroup's TMEM columns, pre-reduces it into that tile's stage and adds the distinct values to
+// y, so the scatter no longer sits on the compute warpgroups' critical path.  Per compute
+// warpgroup five mbarriers order the hand-offs, each completing once per tile:
+//   g1: GEMM 1 done (compute);  g2: GEMM 2 done (compute, scatter);  rdy: tile's stage ready for
+//   the scatter;  yfree: Y' read by the scatter (GEMM 2 of the next tile may overwrite it);
+//   stfree: the tile's stage flushed (it may be refilled).
+// The scatter warpgroup visits tiles in the compute warpgroups' round-robin order; every signal is
+// awaited before the next phase of the same barrier can complete, so parities never run two
+// phases ahead.  Waits are bounded (about 1 s) and share an abort flag: once one gives up, every
+// other wait returns at once and all warpgroups leave their loops.
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return false;
+    if (global_ns() - t0 > 1000000000ull) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <int ND, int NQ, bool BF16>
+constexpr int ws_groups() {
+  return tc_max_groups<ND, NQ, BF16, false, false>();
+}
+
+template <int ND, int NQ, bool BF16>
+__global__ void __launch_bounds__(kT * (ws_groups<ND, NQ, BF16>() + 1), 1)
+    k_cg_apply_tc_ws(const int64_t* __restrict__ tl_span, const int32_t* __restrict__ tl_list,
+                     const uint16_t* __restrict__ tl_lidx, const float* __restrict__ metric,
+                     const uint8_t* __restrict__ bimg, const float* __restrict__ u, float* __restrict__ y,
+                     int64_t nc, int64_t ntiles, int lmax, uint32_t tmem_cols, int32_t* __restrict__ status) {
+  using S = TcShape<ND, NQ, BF16>;
+  using St = Stage<ND, NQ, false>;
+  constexpr int NDP = round_up(ND, 2);
+  constexpr int TCOLS = tc_tcols<ND, NQ, BF16, false>();
+  constexpr int kStages = 4;
+  constexpr int IMG_BYTES = S::B1_BYTES + S::B2_BYTES;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int G = blockDim.x / kT - 1;  // compute warpgroups; warpgroup G scatters
+  const int g = threadIdx.x / kT;
+  const int m = threadIdx.x % kT;
+  const int warp = threadIdx.x >> 5;
+  uint8_t* sB1 = smem;
+  uint8_t* sB2 = sB1 + S::B1_BYTES;
+  uint8_t* misc = smem + IMG_BYTES + size_t(G) * S::A1_BYTES;  // [G][64] barriers, then TMEM slot, abort, maxima
+  auto bars = [&](int gg) { return smem_u32(misc + 64 * gg); };  // g1, g2, rdy, yfree, stfree (8 bytes each)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 64 * G);
+  volatile int* abort = reinterpret_cast<volatile int*>(misc + 64 * G + 4);
+  uint32_t* wmax = reinterpret_cast<uint32_t*>(misc + 64 * G + 16);
+  const size_t sbytes = stage_bytes<ND, NQ, false>(lmax);
+  uint8_t* stages = misc + 64 * G + 64;
+  auto stage_of = [&](int gg, int i) {
+    return stage_at<ND, NQ, false>(stages + (size_t(gg) * kStages + i) * sbytes, lmax);
+  };
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(bimg);
+    uint4* dst = reinterpret_cast<uint4*>(sB1);
+    for (int i = threadIdx.x; i < IMG_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+  }
+  if (g < G && m == 0)
+    for (int k = 0; k < 5; ++k) mbar_init(bars(g) + 8 * k);
+  if (threadIdx.x == 0) *abort = 0;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  const int64_t stride = int64_t(gridDim.x) * G;
+  bool failed = false;
+
+  if (g < G) {
+    // ---- compute warpgroup ----
+    uint8_t* sA1 = smem + IMG_BYTES + size_t(g) * S::A1_BYTES;
+    auto stage = [&](int i) { return stage_of(g, i); };
+    const uint32_t b_g1 = bars(g), b_g2 = bars(g) + 8, b_rdy = bars(g) + 16, b_yfree = bars(g) + 24,
+                   b_stfree = bars(g) + 32;
+    int64_t tile = int64_t(blockIdx.x) * G + g;
+    int L_cur = 0, L_next = 0, L_next2 = 0;
+    if (tile < ntiles)
+      L_cur = issue_meta<ND, NQ, false>(stage(0), m, tile, tl_span, tl_list, tl_lidx, nullptr, nc);
+    else
+      cp_async_commit();
+    cp_async_wait_group<0>();
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot + uint32_t(g * TCOLS);
+    const uint32_t lane_base = tmem + (uint32_t((warp & 3) * 32) << 16);
+    const uint32_t aA1 = smem_u32(sA1), aB1 = smem_u32(sB1), aB2 = smem_u32(sB2);
+    if (tile < ntiles) issue_gather<ND, NQ, false>(stage(0), m, L_cur, u);
+    else cp_async_commit();
+    if (tile + stride < ntiles)
+      L_next = issue_meta<ND, NQ, false>(stage(1), m, tile + stride, tl_span, tl_list, tl_lidx, nullptr, nc);
+    else
+      cp_async_commit();
+    cp_async_wait_group<0>();
+    wg_sync(g);
+    if (tile + stride < ntiles) issue_gather<ND, NQ, false>(stage(1), m, L_next, u);
+    else cp_async_commit();
+    if (tile + 2 * stride < ntiles)
+      L_next2 = issue_meta<ND, NQ, false>(stage(2), m, tile + 2 * stride, tl_span, tl_list, tl_lidx, nullptr, nc);
+    else
+      cp_async_commit();
+    int b = 0;
+    for (uint32_t k = 0; tile < ntiles; tile += stride, ++k, b = (b + 1 == kStages ? 0 : b + 1)) {
+      const int bg = (b + 2) % kStages, bm = (b + 3) % kStages;
+      const St cur = stage(b);
+      const int64_t tg = tile + 2 * stride, tm = tile + 3 * stride;
+      const float* mp = metric + tile * 6 * kT + m;
+      const float m0 = __ldg(mp), m1 = __ldg(mp + kT), m2 = __ldg(mp + 2 * kT), m3 = __ldg(mp + 3 * kT),
+                  m4 = __ldg(mp + 4 * kT), m5 = __ldg(mp + 5 * kT);
+      const int L = L_cur;
+      int L_new = 0;
+      // rows of U' (difference form)
+      {
+        uint32_t lw[NDP / 2];
+#pragma unroll
+        for (int w = 0; w < NDP / 2; ++w) lw[w] = cur.lidx[w * kT + m];
+        auto pos = [&](int j) { return (lw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu; };
+        const float ue0 = cur.vals[pos(0)];
+        float v1[S::K1];
+#pragma unroll
+        for (int j = 1; j < ND; ++j) v1[j - 1] = cur.vals[pos(j)] - ue0;
+#pragma unroll
+        for (int j = S::ND1; j < S::K1; ++j) v1[j] = 0.0f;
+        write_row<S::K1, BF16>(sA1, m, v1);
+      }
+      fence_proxy_async();
+      // GEMM 2 of the previous tile must be complete before GEMM 1 overwrites Q
+      if (k > 0 && m == 0) failed |= !mbar_wait_ab(b_g2, (k - 1) & 1, abort);
+      tc_fence_before();
+      failed = wg_any(g, failed);
+      if (failed) break;
+      tc_fence_after();
+      if (m == 0) {
+#pragma unroll
+        for (int s = 0; s < S::K1 / S::KSTEP; ++s)
+          mma<BF16>(tmem, smem_desc(aA1 + s * 2 * S::LBO_A, S::LBO_A, 128),
+                    smem_desc(aB1 + s * 2 * S::LBO_B1, S::LBO_B1, 128), S::idesc(S::N1), s > 0);
+        mma_commit(b_g1);
+      }
+      // the tile's accumulator (its values were read into the rows above)
+      for (int i = m; i < (L + 4) / 4; i += kT)
+        reinterpret_cast<float4*>(cur.vals)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      cp_async_wait_group<0>();  // values of t+1, metadata of t+2 (this thread's share)
+      if (m == 0) failed |= !mbar_wait_ab(b_g1, k & 1, abort);
+      failed = wg_any(g, failed);
+      if (failed) break;
+      tc_fence_after();
+      // gather of t+2; metadata of t+3 into the stage of t-1 once the scatter has flushed it
+      if (tg < ntiles) issue_gather<ND, NQ, false>(stage(bg), m, L_next2, u);
+      else cp_async_commit();
+      if (k > 0) failed |= !mbar_wait_ab(b_stfree, (k - 1) & 1, abort);
+      if (tm < ntiles)
+        L_new = issue_meta<ND, NQ, false>(stage(bm), m, tm, tl_span, tl_list, tl_lidx, nullptr, nc);
+      else
+        cp_async_commit();
+      // TF32 keeps one chunk live at a time (the warp-specialised kernel runs at 128 registers)
+      metric_to_q<ND, NQ, BF16, false, false, false, !BF16>(lane_base, m0, m1, m2, m3, m4, m5, nullptr);
+      tmem_wait_st();
+      tc_fence_before();
+      wg_sync(g);
+      if (m == 0) {
+        // the scatter has read the previous tile's Y' (GEMM 2 overwrites it); then hand this tile over
+        if (k > 0) failed |= !mbar_wait_ab(b_yfree, (k - 1) & 1, abort);
+        mbar_arrive(b_rdy);
+        tc_fence_after();
+#pragma unroll
+        for (int s = 0; s < S::K2 / S::KSTEP; ++s)
+          mma_ta<BF16>(tmem + S::D2_COL, tmem + 8 * s, smem_desc(aB2 + s * 2 * S::LBO_B2, S::LBO_B2, 128),
+                       S::idesc(S::N2), s > 0);
+        mma_commit(b_g2);
+      }
+      L_cur = L_next;
+      L_next = L_next2;
+      L_next2 = L_new;
+    }
+    cp_async_wait_all();
+    failed = wg_any(g, failed);
+  } else {
+    // ---- scatter warpgroup ----
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot + (uint32_t((warp & 3) * 32) << 16);
+    for (uint32_t k = 0; !failed && int64_t(blockIdx.x) * G + int64_t(k) * stride < ntiles; ++k) {
+      for (int gg = 0; gg < G; ++gg) {
+        const int64_t t = int64_t(blockIdx.x) * G + gg + int64_t(k) * stride;
+        if (t >= ntiles) break;
+        const uint32_t bb = bars(gg);
+        bool f = !mbar_wait_ab(bb + 16, k & 1, abort);  // stage ready
+        f = f || !mbar_wait_ab(bb + 8, k & 1, abort);   // GEMM 2 done
+        failed = wg_any(G, f);
+        if (failed) break;
+        tc_fence_after();
+        uint32_t r[S::N2];
+#pragma unroll
+        for (int c = 0; c < S::N2 / 16; ++c) tmem_ld16(tbase + gg * TCOLS + S::D2_COL + 16 * c, r + 16 * c);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < S::N2 / 16; ++c) reg_fence16(r + 16 * c);
+        tc_fence_before();
+        const St st = stage_of(gg, int(k % kStages));
+        uint32_t lw[NDP / 2];
+#pragma unroll
+        for (int w = 0; w < NDP / 2; ++w) lw[w] = st.lidx[w * kT + m];
+        auto pos = [&](int j) { return (lw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu; };
+        const int Ls = int(__ldg(tl_span + 2 * t + 1));
+        float yv[ND];
+        float y0 = 0.0f;
+        uint32_t mx = 0u;
+#pragma unroll
+        for (int j = 1; j < ND; ++j) {
+          yv[j] = __uint_as_float(r[j - 1]);
+          y0 -= yv[j];
+          mx = max(mx, __float_as_uint(fabsf(yv[j])));
+        }
+        yv[0] = y0;
+        mx = max(mx, __float_as_uint(fabsf(y0)));
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if ((m & 31) == 0) wmax[m >> 5] = mx;
+        wg_sync(G);
+        if (m == 0) mbar_arrive(bb + 24);  // Y' read: GEMM 2 of the next tile may overwrite it
+        mx = max(max(wmax[0], wmax[1]), max(wmax[2], wmax[3]));
+        const int E = mx ? max(int((mx >> 23) & 0xFFu) - 126, -100) : 0;
+        if (E <= 128) {
+          const float scale = __int_as_float((127 + 24 - E) << 23);
+          int* iv = reinterpret_cast<int*>(st.vals);
+#pragma unroll
+          for (int j = 0; j < ND; ++j) atomicAdd(iv + pos(j), __float2int_rn(yv[j] * scale));
+          wg_sync(G);
+          const float inv = __int_as_float((127 - 24 + E) << 23);
+          for (int i = m; i < Ls; i += kT) atomicAdd(y + st.list[i], float(iv[i]) * inv);
+        } else {
+#pragma unroll
+          for (int j = 0; j < ND; ++j) atomicAdd(st.vals + pos(j), yv[j]);
+          wg_sync(G);
+          for (int i = m; i < Ls; i += kT) atomicAdd(y + st.list[i], st.vals[i]);
+        }
+        wg_sync(G);  // the flush of this stage is complete (and wmax may be reused)
+        if (m == 0) mbar_arrive(bb + 32);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(tmem_cols));
+  if (failed && m == 0) atomicOr(status, 1);
+}
+
 // TF32 value of v as the image stores it (round to nearest, ties away from zero)
 double tf32_value(double v) {
   float f = float(v);
@@ -516,9 +779,36 @@ int launch_g(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) 
   return FEM_OK;
 }
 
+template <int ND, int NQ, bool BF16>
+int launch_ws(Ctx& c, const float* u, float* y, cudaStream_t st) {
+  using S = TcShape<ND, NQ, BF16>;
+  constexpr int G = ws_groups<ND, NQ, BF16>();
+  const int lmax = round_up(c.tl_max + 1, 4);
+  const size_t sm = size_t(S::B1_BYTES) + S::B2_BYTES + size_t(G) * S::A1_BYTES + 64 * G + 64 +
+                    size_t(G) * 4 * stage_bytes<ND, NQ, false>(lmax);
+  int dev = 0, smem_max = 0;
+  TETMF_CK(cudaGetDevice(&dev));
+  TETMF_CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (sm > size_t(smem_max)) return launch_g<ND, NQ, BF16, false, false, false>(c, u, y, nullptr, st);
+  auto kern = k_cg_apply_tc_ws<ND, NQ, BF16>;
+  if (int e = allow_smem(kern, sm)) return e;
+  const uint32_t cols = uint32_t(pow2_cols(G * tc_tcols<ND, NQ, BF16, false>()));
+  int64_t grid = (c.ntiles + G - 1) / G;
+  if (grid > sm_count()) grid = sm_count();
+  kern<<<unsigned(grid), (G + 1) * kT, sm, st>>>(c.d_tl_span, c.d_tl_list, c.d_tl_lidx, c.d_metric32,
+                                                 static_cast<const uint8_t*>(BF16 ? c.d_tc_bf16 : c.d_tc_tf32), u, y,
+                                                 c.nc, c.ntiles, lmax, cols, c.d_status);
+  TETMF_LAUNCH_CK();
+  return FEM_OK;
+}
+
 template <int ND, int NQ, bool BF16, bool X3>
 int launch(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) {
   if (int e = init_rows<float>(y, u, c.d_mask, c.ndofs, 0.0f, st)) return e;
+  if constexpr (!X3 && ws_groups<ND, NQ, BF16>() <= 3) {
+    // the warp-specialised kernel where TMEM leaves room for at most three tiles per SM
+    if (!k) return launch_ws<ND, NQ, BF16>(c, u, y, st);
+  }
   return k ? launch_g<ND, NQ, BF16, true, X3, false>(c, u, y, k, st)
            : launch_g<ND, NQ, BF16, false, X3, false>(c, u, y, k, st);
 }

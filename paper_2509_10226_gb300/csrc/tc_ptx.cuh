@@ -216,7 +216,9 @@ __device__ __forceinline__ uint64_t splat2(float v) {
 // remainder (exact in FP32, stored at column offset qlo), for the three-product GEMM 2.
 // CURVED: the metric differs per point; qm points at this cell's entry (q, r) = qm[(6 q + r) * 128]
 // and a chunk's 96 values are loaded before its gradients are read from TMEM.
-template <int ND, int NQ, bool BF16, bool HAS_K, bool X3 = false, bool CURVED = false>
+// ROLLED: the chunks are not unrolled (one chunk's 48 values live at a time; for kernels run at
+// 128 registers per thread).
+template <int ND, int NQ, bool BF16, bool HAS_K, bool X3 = false, bool CURVED = false, bool ROLLED = false>
 __device__ __forceinline__ void metric_to_q(uint32_t lane_base, float m0, float m1, float m2, float m3, float m4,
                                             float m5, const float* kq, uint32_t qlo = 0,
                                             const float* __restrict__ qm = nullptr) {
@@ -224,8 +226,7 @@ __device__ __forceinline__ void metric_to_q(uint32_t lane_base, float m0, float 
   constexpr int NCHUNK = (NP + 7) / 8;
   const uint64_t M0 = splat2(m0), M1 = splat2(m1), M2 = splat2(m2), M3 = splat2(m3), M4 = splat2(m4),
                  M5 = splat2(m5);
-#pragma unroll
-  for (int c = 0; c < NCHUNK; ++c) {
+  auto chunk = [&](int c) {
     const int np = (NP - 8 * c) < 8 ? (NP - 8 * c) : 8;  // pairs in this chunk
     const int nl = (6 * np + 15) / 16;                    // x16 loads in this chunk
     float mq[CURVED ? 96 : 1];
@@ -293,6 +294,13 @@ __device__ __forceinline__ void metric_to_q(uint32_t lane_base, float m0, float 
           tmem_st16(lane_base + 48 * c + 16 * l, d + 16 * l);
         }
     }
+  };
+  if constexpr (ROLLED) {
+#pragma unroll 1
+    for (int c = 0; c < NCHUNK; ++c) chunk(c);
+  } else {
+#pragma unroll
+    for (int c = 0; c < NCHUNK; ++c) chunk(c);
   }
 }
 
