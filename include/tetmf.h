@@ -201,6 +201,19 @@ int fem_device_status(fem_ctx* ctx, int32_t* status);
  * (EINVAL otherwise).  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
 int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k, void* stream);
 
+/* y_host[b] = A u_host[b] for b = 0..nvec-1 with HOST vectors (a stream of
+ * requests): u_host, y_host are arrays of nvec host pointers, each to N values
+ * (double for FEM_FP64, float otherwise) in library order; no coefficient.
+ * The same buffer may appear several times; page-locked (pinned) memory gives
+ * the full link bandwidth.  The vectors pass through two device input and two
+ * device output buffers owned by the context (allocated on the first call and
+ * kept until fem_destroy): the copy of vector b+1 in, the apply of vector b
+ * and the copy of vector b-1 out run concurrently on three streams of the
+ * context.  The operator is fem_apply's (Eq. 3, Eq. 5).  Blocking: returns
+ * when every y_host[b] is written.  Errors: EINVAL (nvec < 1, a null
+ * pointer), EUNSUPPORTED, ENOMEM, ECUDA. */
+int fem_apply_host(fem_ctx* ctx, int32_t prec, int64_t nvec, const void* const* u_host, void* const* y_host);
+
 /* Vector Laplacian with ncomp (1..8) independent components, y_c = A u_c
  * (the vector-valued Poisson problem of Sec. 3.1): u, y are [ncomp][N]
  * component-major device arrays.  FEM_FP64 / FEM_FP32 run components-batched

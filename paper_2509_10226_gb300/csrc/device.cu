@@ -187,6 +187,7 @@ int device_status(Ctx& c, int32_t* out) {
 
 void release(Ctx& c) {
   pmg_release(c);
+  host_pipe_release(c);
   if (c.device >= 0 && !c.allocations.empty()) {
     cudaSetDevice(c.device);
     cudaDeviceSynchronize();

@@ -109,6 +109,7 @@ struct Ctx {
   size_t work_bytes = 0;
 
   void* pmg = nullptr;               // p-multigrid hierarchy of the solver (pmg.cu), built on first use
+  void* host_pipe = nullptr;         // buffers and streams of fem_apply_host (host.cu), built on first use
   std::vector<void*> allocations;   // every cudaMalloc, freed by destroy
 };
 
@@ -150,6 +151,9 @@ int pmg_setup(Ctx& c, int prec, const float* diag, int degree, int coarse_steps,
 int pmg_inner_solve(Ctx& c, const float* diag, float* r, float* d, float* p, float* q, double rtol, int max_it,
                     int& iters, void* stream);
 void pmg_release(Ctx& c);
+// host-buffer apply (host.cu): y_host[b] = A u_host[b], b < nvec, blocking
+int apply_host(Ctx& c, int prec, int64_t nvec, const void* const* u_host, void* const* y_host);
+void host_pipe_release(Ctx& c);
 // p-transfer (transfer.cu)
 struct Transfer;
 int transfer_create(Ctx& fine, Ctx& coarse, Transfer** out);

@@ -884,6 +884,18 @@ int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k,
   }
 }
 
+int fem_apply_host(fem_ctx* ctx, int32_t prec, int64_t nvec, const void* const* u_host, void* const* y_host) {
+  if (int s = check_device(ctx)) return s;
+  if (nvec < 1 || !u_host || !y_host) return set_error("fem_apply_host: nvec >= 1 and pointer arrays required"), FEM_EINVAL;
+  for (int64_t b = 0; b < nvec; ++b)
+    if (!u_host[b] || !y_host[b]) return set_error("fem_apply_host: null vector %lld", (long long)b), FEM_EINVAL;
+  Ctx& c = ctx->c;
+  if (c.kind == FEM_DG && prec == FEM_TF32X3)
+    return set_error("fem_apply_host: FEM_TF32X3 is offered for CG only"), FEM_EUNSUPPORTED;
+  if (prec < FEM_FP64 || prec > FEM_TF32X3) return set_error("fem_apply_host: unknown precision %d", prec), FEM_EUNSUPPORTED;
+  return apply_host(c, prec, nvec, u_host, y_host);
+}
+
 int fem_apply_adjoint(fem_ctx* ctx, int32_t prec, const void* g, void* out, const void* k, void* stream) {
   if (int s = check_device(ctx)) return s;
   if (!g || !out || g == out) return set_error("fem_apply_adjoint: g and out must be distinct non-null"), FEM_EINVAL;

@@ -148,6 +148,23 @@ class FemSpace:
         call("fem_apply", self._h, PREC[prec], _ptr(u), _ptr(y), _ptr(k), _stream(stream))
         return y
 
+    def apply_host(self, us, ys, prec="fp64"):
+        """ys[b] = A us[b] for host (CPU) tensors us[b], ys[b] of n_dofs values (a stream of
+        requests through the device; blocking).  Pinned tensors give the full link bandwidth; a
+        tensor may appear several times in ys (its last vector wins)."""
+        if len(us) != len(ys) or not us:
+            raise ValueError("us and ys must be equally long, non-empty sequences")
+        dt = _vec_dtype(prec)
+        for t in list(us) + list(ys):
+            if not (isinstance(t, torch.Tensor) and not t.is_cuda and t.dtype == dt and t.is_contiguous()
+                    and t.numel() == self.n_dofs):
+                raise ValueError("host vectors must be contiguous CPU tensors of n_dofs values of the precision's type")
+        n = len(us)
+        up = (ctypes.c_void_p * n)(*[t.data_ptr() for t in us])
+        yp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in ys])
+        call("fem_apply_host", self._h, PREC[prec], n, up, yp)
+        return ys
+
     def apply_vector(self, u, prec="fp64", out=None, stream=None):
         """y[c] = A u[c] for the components c of u [ncomp, N] (vector Laplacian)."""
         if not (isinstance(u, torch.Tensor) and u.is_cuda and u.dim() == 2 and u.shape[1] == self.n_dofs
