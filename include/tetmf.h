@@ -210,7 +210,8 @@ int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k,
  * kept until fem_destroy): the copy of vector b+1 in, the apply of vector b
  * and the copy of vector b-1 out run concurrently on three streams of the
  * context.  The operator is fem_apply's (Eq. 3, Eq. 5).  Blocking: returns
- * when every y_host[b] is written.  Errors: EINVAL (nvec < 1, a null
+ * when every y_host[b] is written; one call at a time per context (the slots
+ * and streams are the context's).  Errors: EINVAL (nvec < 1, a null
  * pointer), EUNSUPPORTED, ENOMEM, ECUDA. */
 int fem_apply_host(fem_ctx* ctx, int32_t prec, int64_t nvec, const void* const* u_host, void* const* y_host);
 
