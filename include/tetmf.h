@@ -191,6 +191,17 @@ int fem_dirichlet_mask(const fem_ctx* ctx, uint8_t* mask);
  * returned without finishing its tiles.  Kernels never trap. */
 int fem_device_status(fem_ctx* ctx, int32_t* status);
 
+/* Diagnostics of the bounded waits (no GPU fault involved): runs one CTA of
+ * two warpgroups that allocates TMEM and then waits, through the tensor-core
+ * kernels' own wait helper, on two mbarriers that nothing completes.  The
+ * first wait gives up after limit_ns (1e3..2e9) and raises the CTA's abort
+ * flag, the other returns at once; the CTA frees its TMEM and sets bit 0 of the
+ * device status word, exactly as an apply kernel that gave up would.
+ * waited_ns[0..1] receive the two waits' durations.  Blocking (synchronises
+ * the device); the context stays usable.  Read the word with
+ * fem_device_status. */
+int fem_selftest_wait(fem_ctx* ctx, int64_t limit_ns, int64_t* waited_ns);
+
 /* ---- hot calls (asynchronous on `stream`, allocate nothing) -------- */
 
 /* y = A(k) u.  u, y: device vectors of N values (double for FEM_FP64, float

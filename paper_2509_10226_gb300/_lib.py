@@ -77,6 +77,7 @@ _SIGNATURES = {
     "fem_smoother_work_bytes": [_P, ctypes.c_int32, _P],
     "fem_dirichlet_mask": [_P, _P],
     "fem_device_status": [_P, _P],
+    "fem_selftest_wait": [_P, ctypes.c_int64, _P],
     "fem_apply": [_P, ctypes.c_int32, _P, _P, _P, _P],
     "fem_apply_host": [_P, ctypes.c_int32, ctypes.c_int64, _P, _P],
     "fem_apply_adjoint": [_P, ctypes.c_int32, _P, _P, _P, _P],

@@ -440,21 +440,6 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3, CURVED>()
 // awaited before the next phase of the same barrier can complete, so parities never run two
 // phases ahead.  Waits are bounded (about 1 s) and share an abort flag: once one gives up, every
 // other wait returns at once and all warpgroups leave their loops.
-__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int* abort) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort) return false;
-    if (global_ns() - t0 > 1000000000ull) {
-      *abort = 1;
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 
 template <int ND, int NQ, bool BF16>
 constexpr int ws_groups() {

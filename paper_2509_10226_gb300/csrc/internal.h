@@ -154,6 +154,8 @@ void pmg_release(Ctx& c);
 // host-buffer apply (host.cu): y_host[b] = A u_host[b], b < nvec, blocking
 int apply_host(Ctx& c, int prec, int64_t nvec, const void* const* u_host, void* const* y_host);
 void host_pipe_release(Ctx& c);
+// bounded-wait diagnostics (selftest.cu): waits that nothing completes give up after limit_ns
+int selftest_wait(Ctx& c, int64_t limit_ns, int64_t* waited_ns);
 // p-transfer (transfer.cu)
 struct Transfer;
 int transfer_create(Ctx& fine, Ctx& coarse, Transfer** out);

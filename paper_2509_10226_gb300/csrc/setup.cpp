@@ -884,6 +884,13 @@ int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k,
   }
 }
 
+int fem_selftest_wait(fem_ctx* ctx, int64_t limit_ns, int64_t* waited_ns) {
+  if (int s = check_device(ctx)) return s;
+  if (limit_ns < 1000 || limit_ns > 2000000000 || !waited_ns)
+    return set_error("fem_selftest_wait: limit_ns in [1e3, 2e9] and an output array required"), FEM_EINVAL;
+  return selftest_wait(ctx->c, limit_ns, waited_ns);
+}
+
 int fem_apply_host(fem_ctx* ctx, int32_t prec, int64_t nvec, const void* const* u_host, void* const* y_host) {
   if (int s = check_device(ctx)) return s;
   if (nvec < 1 || !u_host || !y_host) return set_error("fem_apply_host: nvec >= 1 and pointer arrays required"), FEM_EINVAL;

@@ -129,6 +129,13 @@ class FemSpace:
         call("fem_device_status", self._h, ctypes.byref(v))
         return v.value
 
+    def selftest_wait(self, limit_s=0.05):
+        """Run the bounded-wait diagnostics (waits that nothing completes give up after limit_s);
+        returns the two waits' durations in seconds.  Sets bit 0 of the device status word."""
+        w = (ctypes.c_int64 * 2)()
+        call("fem_selftest_wait", self._h, int(limit_s * 1e9), w)
+        return w[0] * 1e-9, w[1] * 1e-9
+
     # ---- hot calls -------------------------------------------------------
     def _check_vec(self, t, prec, name, n=None):
         n = self.n_dofs if n is None else n
