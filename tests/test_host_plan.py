@@ -149,3 +149,20 @@ def test_host_only_plan_rejects_device_calls():
     L = _lib.lib()
     assert L.fem_apply(sp._h, 0, 1, 2, None, None) == _lib.FEM_EINVAL
     assert b"host-only" in L.fem_last_error()
+
+
+def test_host_only_plan_rejects_host_buffer_and_diagnostic_calls():
+    import ctypes
+
+    xyz, cells = synth.kuhn_cube(2)
+    sp = space(xyz, cells, degree=1)
+    L = _lib.lib()
+    u = np.zeros(sp.n_dofs, dtype=np.float32)
+    ptrs = (ctypes.c_void_p * 1)(u.ctypes.data)
+    assert L.fem_apply_host(sp._h, _lib.FEM_FP32, 1, ptrs, ptrs) == _lib.FEM_EINVAL
+    assert b"host-only" in L.fem_last_error()
+    waited = (ctypes.c_int64 * 2)()
+    assert L.fem_selftest_wait(sp._h, 1000000, waited) == _lib.FEM_EINVAL
+    assert b"host-only" in L.fem_last_error()
+    # argument checks come before any device work as well
+    assert L.fem_apply_host(None, _lib.FEM_FP32, 1, ptrs, ptrs) == _lib.FEM_EINVAL
