@@ -40,9 +40,11 @@
  *
  * Streams.  Hot calls are asynchronous on the caller's CUDA stream, passed as
  * void* (a cudaStream_t; NULL = legacy default stream).  They allocate
- * nothing and never synchronise, except fem_solve (blocking, see there).
- * Vector pointers of hot calls are caller-owned device memory of the
- * context's device.  A context is not thread-safe; distinct contexts are
+ * nothing and never synchronise.  The calls documented as blocking
+ * (fem_solve, fem_lambda_max, fem_apply_host, fem_selftest_wait) return
+ * with their work complete.  Vector pointers of hot calls are caller-owned
+ * device memory of the context's device; fem_apply_host takes host
+ * pointers.  A context is not thread-safe; distinct contexts are
  * independent.
  */
 #ifndef TETMF_H
@@ -212,20 +214,6 @@ int fem_selftest_wait(fem_ctx* ctx, int64_t limit_ns, int64_t* waited_ns);
  * (EINVAL otherwise).  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
 int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k, void* stream);
 
-/* y_host[b] = A u_host[b] for b = 0..nvec-1 with HOST vectors (a stream of
- * requests): u_host, y_host are arrays of nvec host pointers, each to N values
- * (double for FEM_FP64, float otherwise) in library order; no coefficient.
- * The same buffer may appear several times; page-locked (pinned) memory gives
- * the full link bandwidth.  The vectors pass through two device input and two
- * device output buffers owned by the context (allocated on the first call and
- * kept until fem_destroy): the copy of vector b+1 in, the apply of vector b
- * and the copy of vector b-1 out run concurrently on three streams of the
- * context.  The operator is fem_apply's (Eq. 3, Eq. 5).  Blocking: returns
- * when every y_host[b] is written; one call at a time per context (the slots
- * and streams are the context's).  Errors: EINVAL (nvec < 1, a null
- * pointer), EUNSUPPORTED, ENOMEM, ECUDA. */
-int fem_apply_host(fem_ctx* ctx, int32_t prec, int64_t nvec, const void* const* u_host, void* const* y_host);
-
 /* Vector Laplacian with ncomp (1..8) independent components, y_c = A u_c
  * (the vector-valued Poisson problem of Sec. 3.1): u, y are [ncomp][N]
  * component-major device arrays.  FEM_FP64 / FEM_FP32 run components-batched
@@ -250,6 +238,22 @@ int fem_diagonal(fem_ctx* ctx, int32_t prec, void* d, const void* k, void* strea
 
 /* b_i = int f phi_i for a constant f (CG; FP64; Dirichlet entries 0). */
 int fem_rhs_const(fem_ctx* ctx, double f, double* b, void* stream);
+
+/* ---- host-buffer apply (blocking) ---------------------------------- */
+
+/* y_host[b] = A u_host[b] for b = 0..nvec-1 with HOST vectors (a stream of
+ * requests): u_host, y_host are arrays of nvec host pointers, each to N values
+ * (double for FEM_FP64, float otherwise) in library order; no coefficient.
+ * The same buffer may appear several times; page-locked (pinned) memory gives
+ * the full link bandwidth.  The vectors pass through two device input and two
+ * device output buffers owned by the context (allocated on the first call and
+ * kept until fem_destroy): the copy of vector b+1 in, the apply of vector b
+ * and the copy of vector b-1 out run concurrently on three streams of the
+ * context.  The operator is fem_apply's (Eq. 3, Eq. 5).  Blocking: returns
+ * when every y_host[b] is written; one call at a time per context (the slots
+ * and streams are the context's).  Errors: EINVAL (nvec < 1, a null
+ * pointer), EUNSUPPORTED, ENOMEM, ECUDA. */
+int fem_apply_host(fem_ctx* ctx, int32_t prec, int64_t nvec, const void* const* u_host, void* const* y_host);
 
 /* ---- smoother (Chebyshev-Jacobi, the smoother of Sec. 4.1's multigrid) */
 
