@@ -166,3 +166,25 @@ def test_host_only_plan_rejects_host_buffer_and_diagnostic_calls():
     assert b"host-only" in L.fem_last_error()
     # argument checks come before any device work as well
     assert L.fem_apply_host(None, _lib.FEM_FP32, 1, ptrs, ptrs) == _lib.FEM_EINVAL
+
+
+def test_apply_host_binding_checks_arguments_before_the_call():
+    import torch
+
+    xyz, cells = synth.kuhn_cube(2)
+    sp = space(xyz, cells, degree=1)
+    good = torch.zeros(sp.n_dofs, dtype=torch.float32)
+    with pytest.raises(ValueError):
+        sp.apply_host([], [], prec="fp32")                      # empty
+    with pytest.raises(ValueError):
+        sp.apply_host([good, good], [good], prec="fp32")        # lengths differ
+    with pytest.raises(ValueError):
+        sp.apply_host([good], [good.double()], prec="fp32")     # wrong vector type
+    with pytest.raises(ValueError):
+        sp.apply_host([good[:-1].contiguous()], [good], prec="fp32")  # wrong length
+    with pytest.raises(ValueError):
+        sp.apply_host([torch.zeros(2 * sp.n_dofs)[::2]], [good], prec="fp32")  # not contiguous
+    # well-formed arguments reach the library, which refuses a host-only context
+    with pytest.raises(FemError) as e:
+        sp.apply_host([good], [good], prec="fp32")
+    assert e.value.status == _lib.FEM_EINVAL
