@@ -9,7 +9,11 @@ HBM; the L2 is flushed (a 256 MiB write) before every timed step, outside the
 timed events.  `value` is the TF32 tensor-core apply in GDoF/s (DoFs / s,
 Sec. 2.3); the FP64, FP32 and BF16 applies, the assembled CSR SpMV of the same
 operator and the DG SIPG P2 apply on the 48^3 cube are reported under
-`variants`.
+`variants`.  `e2e` is the same apply through the host-buffer call
+(fem_apply_host): every step copies its input from pinned host memory and its
+result back inside the timed region, one call streaming all steps (copy in,
+apply and copy out overlapped on three streams); `serial_value` makes one
+blocking call per step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
