@@ -251,6 +251,39 @@ def time_solves(torch, FemSpace, device):
     return out
 
 
+def time_solve_sweep(torch, FemSpace, device):
+    """The solve of time_solves for p = 1..4 on the 48^3 cube (117,649 / 912,673 / 3,048,625 /
+    7,189,057 DoFs): FP64 refinement around the TF32 inner Jacobi-PCG and (p >= 2) around the
+    p-multigrid cycle, against the all-FP64 Jacobi-PCG; wall time of each solve after a short warm-up."""
+    xyz, cells = synth.kuhn_cube(48, jitter=0.2, seed=synth.SEEDS["jitter"])
+    out = {"rtol": 1e-10}
+    for p in (1, 2, 3, 4):
+        sp = FemSpace(xyz, cells, kind="cg", degree=p, dirichlet=True, device=device)
+        b = sp.rhs_const(1.0)
+        modes = [("ir_tf32", "ir", "tf32", 0, 0)]
+        if p >= 2:
+            modes.append(("ir_pmg_tf32", "pmg", "tf32", 5, 20))
+        modes.append(("pcg_fp64", "pcg", "fp32", 0, 0))
+        for _, mode, inner, deg, cs in modes[:-1]:  # warm-up (and the p-hierarchy)
+            sp.solve(b, mode=mode, inner_prec=inner, rtol=1e-3, raise_on_notconv=False, smoother_degree=deg,
+                     coarse_steps=cs)
+        row = {"n_dofs": sp.n_dofs}
+        for name, mode, inner, deg, cs in modes:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = sp.solve(b, mode=mode, inner_prec=inner, rtol=1e-10, inner_rtol=1e-3, raise_on_notconv=False,
+                             smoother_degree=deg, coarse_steps=cs)
+            torch.cuda.synchronize()
+            row[name] = {"seconds": time.perf_counter() - t0, "outer": st["outer"], "inner": st["inner"],
+                         "rel_residual": st["rel_residual"], "converged": st["converged"]}
+        best = min(row[n]["seconds"] for n in row if n.startswith("ir"))
+        row["speedup_best_mixed_vs_fp64"] = row["pcg_fp64"]["seconds"] / best
+        out[f"p{p}"] = row
+        del sp, b
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the oracle on the host cores, each step a bounded sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -307,6 +340,8 @@ def main():
     ap.add_argument("--no-transfer", action="store_true", help="skip the p-transfer variants")
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--solve-sweep", action="store_true",
+                    help="also time the 48^3 Dirichlet solve for p = 1..4 (about a minute; off by default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -600,6 +635,11 @@ def main():
                 del dsp
             except Exception as e:  # noqa: BLE001
                 variants["dg_p2_48"] = {"unavailable": str(e).splitlines()[0]}
+    if args.solve_sweep:
+        try:
+            variants["solve_sweep_48"] = time_solve_sweep(torch, FemSpace, local)
+        except Exception as e:  # noqa: BLE001
+            variants["solve_sweep_48"] = {"unavailable": str(e).splitlines()[0]}
     clk = clocks.stop()
     status = sp.device_status()
 

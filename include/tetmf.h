@@ -321,13 +321,16 @@ typedef struct {
   double rtol;           /* stop when ||b - A x|| / ||b|| <= rtol (FP64)     */
   double inner_rtol;     /* IR: relative reduction asked of each inner solve */
   int32_t max_outer;     /* IR outer iterations cap                          */
-  int32_t max_inner;     /* PCG iterations cap (per inner solve for IR)      */
+  int32_t max_inner;     /* PCG iterations cap (per inner solve for IR, in   */
+                         /* total for FP64_PCG)                              */
   int32_t smoother_degree; /* IR_PMG: Chebyshev steps per smoothing (0: 5)   */
   int32_t coarse_steps;  /* IR_PMG: coarse Jacobi-PCG steps (0: 20)          */
 } fem_solve_opts;
 
 typedef struct {
-  int32_t outer_iterations;
+  int32_t outer_iterations;  /* IR: refinement steps; FP64_PCG: PCG passes (a */
+                             /* pass restarts from the true residual b - A x  */
+                             /* when rounding left it above rtol)             */
   int32_t inner_iterations;  /* total PCG iterations                        */
   double rel_residual;       /* final ||b - A x|| / ||b|| computed in FP64   */
   double seconds;

@@ -222,13 +222,21 @@ static int solve_with(Ctx& c, Work& w, const fem_solve_opts* o, const double* b,
     auto apply64 = [&](double* in, double* out) {
       return cg_apply_simt(c, FEM_FP64, in, out, nullptr, false, stream);
     };
-    int it = 0;
-    const int e = pcg<double>(c, w, apply64, x, w.r64, w.z64, w.p64, w.t64, w.diag64, o->rtol * o->rtol * bb,
-                              o->max_inner, it, st);
-    stats->inner_iterations = it;
-    stats->outer_iterations = 1;
-    if (e && e != FEM_ENOTCONV) return e;
-    if (int e2 = residual(rel)) return e2;
+    // PCG stops on its recurrence residual; the true residual b - A x is then recomputed, and where
+    // rounding has left it above the tolerance PCG restarts from x with it (at most 8 restarts,
+    // within the same iteration cap)
+    int total = 0;
+    for (int pass = 0;; ++pass) {
+      int it = 0;
+      const int e = pcg<double>(c, w, apply64, x, w.r64, w.z64, w.p64, w.t64, w.diag64, o->rtol * o->rtol * bb,
+                                o->max_inner - total, it, st);
+      total += it;
+      stats->inner_iterations = total;
+      stats->outer_iterations = pass + 1;
+      if (e && e != FEM_ENOTCONV) return e;
+      if (int e2 = residual(rel)) return e2;
+      if (rel <= o->rtol || e == FEM_ENOTCONV || total >= o->max_inner || pass >= 8 || !std::isfinite(rel)) break;
+    }
     return finish(rel <= o->rtol ? FEM_OK : FEM_ENOTCONV, rel);
   }
 
