@@ -144,7 +144,8 @@ typedef struct {
 /* Validate the mesh, build the plan (reordering, DoF numbering, geometry,
  * reference tables, faces) in FP64 on the host and upload it to `device`.
  * Sec. 2.3-2.5.  On success *out owns every internal buffer.
- * Errors: EINVAL (null pointers, n_cells < 1, bad enum), EUNSUPPORTED
+ * Errors: EINVAL (null pointers, n_cells outside [1, 2^25 - 1], n_vertices
+ * outside [4, 2^31), bad enum), EUNSUPPORTED
  * (degree), EMESH (vertex id out of range, |det J| <= 1e-12 * (longest edge)^3,
  * non-manifold face), ENOMEM, ECUDA. */
 int fem_create(const fem_mesh_desc* mesh, const fem_space_desc* space, fem_ctx** out);

@@ -188,3 +188,20 @@ def test_apply_host_binding_checks_arguments_before_the_call():
     with pytest.raises(FemError) as e:
         sp.apply_host([good], [good], prec="fp32")
     assert e.value.status == _lib.FEM_EINVAL
+
+
+def test_empty_and_oversized_meshes_are_rejected():
+    xyz, cells = synth.kuhn_cube(1)
+    for kind in ("cg", "dg"):
+        with pytest.raises(FemError) as e:
+            space(xyz, np.zeros((0, 4), dtype=np.int32), kind=kind, degree=2)
+        assert e.value.status == _lib.FEM_EINVAL
+    with pytest.raises(FemError) as e:
+        space(np.zeros((0, 3)), np.zeros((0, 4), dtype=np.int32), degree=1)
+    assert e.value.status == _lib.FEM_EINVAL
+    # a cell count above the documented limit is refused before any array is read
+    import ctypes
+    desc = _lib.MeshDesc(4, xyz.ctypes.data, 1 << 25, cells.ctypes.data, None)
+    sd = _lib.SpaceDesc(_lib.FEM_CG, 1, 0, 1, 0.0, -1, 0, 0)
+    h = ctypes.c_void_p()
+    assert _lib.lib().fem_create(ctypes.byref(desc), ctypes.byref(sd), ctypes.byref(h)) == _lib.FEM_EINVAL
