@@ -44,7 +44,9 @@
  * (fem_solve, fem_lambda_max, fem_apply_host, fem_selftest_wait) return
  * with their work complete.  Vector pointers of hot calls are caller-owned
  * device memory of the context's device; fem_apply_host takes host
- * pointers.  A context is not thread-safe; distinct contexts are
+ * pointers.  Every device call checks that the calling thread's current
+ * device is the context's device and returns FEM_EINVAL before anything is
+ * launched otherwise.  A context is not thread-safe; distinct contexts are
  * independent.
  */
 #ifndef TETMF_H
@@ -205,6 +207,17 @@ int fem_device_status(fem_ctx* ctx, int32_t* status);
  * fem_device_status. */
 int fem_selftest_wait(fem_ctx* ctx, int64_t limit_ns, int64_t* waited_ns);
 
+/* Arithmetic-throughput probe (no counterpart in the paper; it measures the
+ * denominators of the FP64 and FP32 rooflines the SIMT applies are reported
+ * against).  Launches 4 x (SM count) blocks of 256 threads on the current
+ * device, each thread running `iters` (1..2^30) iterations of eight
+ * independent FMA chains: kind 0 = FP64 fma, 1 = FP32 fma, 2 = packed FP32x2
+ * fma.  *flops (host) receives the floating-point operations launched (an FMA
+ * counts 2).  sink: device double[1], written only in a case that cannot occur
+ * (it keeps the compiler from removing the loop).  Asynchronous on `stream`;
+ * time it with events.  Errors: EINVAL, ECUDA. */
+int fem_fma_probe(int32_t kind, int64_t iters, double* sink, double* flops, void* stream);
+
 /* ---- hot calls (asynchronous on `stream`, allocate nothing) -------- */
 
 /* y = A(k) u.  u, y: device vectors of N values (double for FEM_FP64, float
@@ -360,10 +373,14 @@ int fem_solve(fem_ctx* ctx, const fem_solve_opts* opts, const double* b, double*
  *     library, reserved on every GPU where the library's device code is
  *     loaded until the process exits; N > FEM_SOLVE_NOALLOC_MAX_DOFS is
  *     rejected with FEM_EINVAL before anything runs;
- *   - the first call on a device looks the array's address up
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture on the device;
- *   - the calling thread's current device must be the context's device;
+ *   - the first call on each context looks the array's address up
+ *     (cudaGetSymbolAddress, with the context's device current) and keeps it
+ *     in the context; make that first call before any stream capture on the
+ *     device.  A device reset (cudaDeviceReset) frees the array together with
+ *     every context's buffers: contexts created afterwards look the new
+ *     address up, and contexts from before the reset must not be used again;
+ *   - the calling thread's current device must be the context's device (as
+ *     for every device call);
  *   - all calls share the one array and each call overwrites it: calls that
  *     overlap on the GPU (other streams, threads or contexts) race and must be
  *     serialised by the caller.

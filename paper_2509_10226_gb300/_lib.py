@@ -88,6 +88,7 @@ _SIGNATURES = {
     "fem_csr_apply": [_P, ctypes.c_int32, _P, _P, _P],
     "fem_solve": [_P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(SolveStats), _P],
     "fem_solve_noalloc": [_P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(SolveStats), _P],
+    "fem_fma_probe": [ctypes.c_int32, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double), _P],
 }
 FEM_SOLVE_NOALLOC_MAX_DOFS = 262144
 

@@ -110,6 +110,8 @@ struct Ctx {
 
   void* pmg = nullptr;               // p-multigrid hierarchy of the solver (pmg.cu), built on first use
   void* host_pipe = nullptr;         // buffers and streams of fem_apply_host (host.cu), built on first use
+  void* noalloc_work = nullptr;      // device address of the static work array of fem_solve_noalloc (solve.cu),
+                                     // looked up by the first such call on this context
   std::vector<void*> allocations;   // every cudaMalloc, freed by destroy
 };
 
@@ -118,6 +120,10 @@ struct TableLayout {
   int64_t E, w, V, wf, Vf, Ef, total;
 };
 TableLayout tables_layout(const RefTables& t);
+
+// argument check of every device entry point (setup.cpp): a context on a device, and that device
+// current on the calling thread; FEM_EINVAL (or FEM_ECUDA) with the message set otherwise
+int check_device(const fem_ctx* ctx);
 
 // set-up steps implemented in .cu files
 int upload(Ctx& c);

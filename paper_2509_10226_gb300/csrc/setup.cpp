@@ -12,6 +12,8 @@
 #include <numeric>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "internal.h"
 
 namespace tetmf {
@@ -535,16 +537,30 @@ int check_ctx(const fem_ctx* ctx) {
   return FEM_OK;
 }
 
+}  // namespace
+
+// device calls run on the calling thread's current device: it must be the context's device, since
+// the context's buffers, the caller's stream and every launch have to live on one GPU
 int check_device(const fem_ctx* ctx) {
   if (int s = check_ctx(ctx)) return s;
   if (ctx->c.device < 0) {
     set_error("host-only context (device = -1) cannot run device calls");
     return FEM_EINVAL;
   }
+  int dev = -1;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaGetDevice failed: %s", cudaGetErrorString(e));
+    return FEM_ECUDA;
+  }
+  if (dev != ctx->c.device) {
+    set_error("the calling thread's current device %d is not the context's device %d", dev, ctx->c.device);
+    return FEM_EINVAL;
+  }
   return FEM_OK;
 }
 
-}  // namespace
 }  // namespace tetmf
 
 namespace tetmf {

@@ -19,7 +19,6 @@
 // beta) stay on the device; the host reads one residual norm per iteration.
 #include <chrono>
 #include <cmath>
-#include <mutex>
 
 #include "blas.cuh"
 #include "common.cuh"
@@ -143,8 +142,8 @@ int read_scalar(const double* dev, double* host, double& out, cudaStream_t st) {
 // Jacobi-PCG on vectors of type T with the operator `apply` (y = A x);
 // solves A x = r starting from x = 0 (r is overwritten by the residual).
 template <typename T, typename Apply>
-int pcg(Ctx& c, Work& w, Apply apply, T* x, T* r, T* z, T* p, T* q, const T* diag, double rtol_abs2, int max_it,
-        int& iters, cudaStream_t st) {
+int pcg(const char* who, Ctx& c, Work& w, Apply apply, T* x, T* r, T* z, T* p, T* q, const T* diag,
+        double rtol_abs2, int max_it, int& iters, cudaStream_t st) {
   const int64_t N = c.ndofs;
   const int rg = red_grid(N), eg = ew_grid(N);
   k_pcg_start<T><<<rg, kBlock, 0, st>>>(r, diag, z, p, N, w.partials, w.ticket, w.scal + S_RZ0, w.scal + S_RR);
@@ -168,7 +167,7 @@ int pcg(Ctx& c, Work& w, Apply apply, T* x, T* r, T* z, T* p, T* q, const T* dia
     if (iters % kCheck != 0 && iters < max_it) continue;
     if (int e = read_scalar(w.scal + S_RR, w.host_scal, rr, st)) return e;
     if (!std::isfinite(rr)) {
-      set_error("fem_solve: residual is not finite after %d iterations", iters);
+      set_error("%s: residual is not finite after %d iterations", who, iters);
       return FEM_ENOTCONV;
     }
   }
@@ -178,8 +177,9 @@ int pcg(Ctx& c, Work& w, Apply apply, T* x, T* r, T* z, T* p, T* q, const T* dia
 }  // namespace
 
 // the solver proper, on work arrays laid out by carve()
-static int solve_with(Ctx& c, Work& w, const fem_solve_opts* o, const double* b, double* x, fem_solve_stats* stats,
-               void* stream) {
+// who: the entry point's name, for the error messages
+static int solve_with(const char* who, Ctx& c, Work& w, const fem_solve_opts* o, const double* b, double* x,
+                      fem_solve_stats* stats, void* stream) {
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = as_stream(stream);
   const int64_t N = c.ndofs;
@@ -189,7 +189,7 @@ static int solve_with(Ctx& c, Work& w, const fem_solve_opts* o, const double* b,
     stats->rel_residual = rel;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (status == FEM_ENOTCONV)
-      set_error("fem_solve: relative residual %.3e above rtol %.3e after %d outer / %d inner iterations", rel,
+      set_error("%s: relative residual %.3e above rtol %.3e after %d outer / %d inner iterations", who, rel,
                 o->rtol, stats->outer_iterations, stats->inner_iterations);
     return status;
   };
@@ -228,7 +228,7 @@ static int solve_with(Ctx& c, Work& w, const fem_solve_opts* o, const double* b,
     int total = 0;
     for (int pass = 0;; ++pass) {
       int it = 0;
-      const int e = pcg<double>(c, w, apply64, x, w.r64, w.z64, w.p64, w.t64, w.diag64, o->rtol * o->rtol * bb,
+      const int e = pcg<double>(who, c, w, apply64, x, w.r64, w.z64, w.p64, w.t64, w.diag64, o->rtol * o->rtol * bb,
                                 o->max_inner - total, it, st);
       total += it;
       stats->inner_iterations = total;
@@ -266,7 +266,7 @@ static int solve_with(Ctx& c, Work& w, const fem_solve_opts* o, const double* b,
     TETMF_LAUNCH_CK();
     int it = 0;
     const int e = pmg ? pmg_inner_solve(c, w.diag32, r32, d32, p32, q32, inner, o->max_inner, it, stream)
-                      : pcg<float>(c, w, apply32, d32, r32, z32, p32, q32, w.diag32, inner * inner, o->max_inner, it,
+                      : pcg<float>(who, c, w, apply32, d32, r32, z32, p32, q32, w.diag32, inner * inner, o->max_inner, it,
                                    st);
     stats->inner_iterations += it;
     stats->outer_iterations += 1;
@@ -279,7 +279,7 @@ static int solve_with(Ctx& c, Work& w, const fem_solve_opts* o, const double* b,
 int solve(Ctx& c, const fem_solve_opts* o, const double* b, double* x, fem_solve_stats* stats, void* stream) {
   Work w;
   if (int e = ensure_work(c, w)) return e;
-  return solve_with(c, w, o, b, x, stats, stream);
+  return solve_with("fem_solve", c, w, o, b, x, stats, stream);
 }
 
 }  // namespace tetmf
@@ -307,17 +307,13 @@ static_assert(5 * 8 + 6 * 4 == 64, "per-DoF work bytes");
 
 static __device__ __align__(256) unsigned char g_noalloc_work[kNoAllocBytes];
 
-std::mutex g_noalloc_mutex;
 void* g_noalloc_addr[64] = {nullptr};
 
-// device address of g_noalloc_work on the current device (looked up once per device)
-int noalloc_address(int dev, void** out) {
-  if (dev < 0 || dev >= 64) {
-    set_error("fem_solve_noalloc: device ordinal %d out of range", dev);
-    return FEM_EINVAL;
-  }
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[dev]) {
+// device address of g_noalloc_work for this context, looked up by the context's first
+// fem_solve_noalloc call with the context's device current.  Keeping it per context (not per
+// device ordinal) means a context created after a device reset looks the address up again.
+int noalloc_address(Ctx& c, void** out) {
+  if (!c.noalloc_work) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_work);
     if (e != cudaSuccess || !p) {
@@ -325,9 +321,9 @@ int noalloc_address(int dev, void** out) {
       set_error("fem_solve_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
       return FEM_ECUDA;
     }
-    g_noalloc_addr[dev] = p;
+    c.noalloc_work = p;
   }
-  *out = g_noalloc_addr[dev];
+  *out = c.noalloc_work;
   return FEM_OK;
 }
 
@@ -337,15 +333,13 @@ int noalloc_address(int dev, void** out) {
 extern "C" int fem_solve_noalloc(fem_ctx* ctx, const fem_solve_opts* opts, const double* b, double* x,
                                  fem_solve_stats* stats, void* stream) {
   using namespace tetmf;
-  if (!ctx || !opts || !b || !x || !stats || (const void*)b == (const void*)x) {
+  // the checks every device entry point makes: a context on a device, and that device current
+  if (int s = check_device(ctx)) return s;
+  if (!opts || !b || !x || !stats || (const void*)b == (const void*)x) {
     set_error("fem_solve_noalloc: null or aliased argument");
     return FEM_EINVAL;
   }
   Ctx& c = ctx->c;
-  if (c.device < 0) {
-    set_error("fem_solve_noalloc: host-only context (device = -1)");
-    return FEM_EINVAL;
-  }
   if (c.kind != FEM_CG) {
     set_error("fem_solve_noalloc: CG spaces only");
     return FEM_EINVAL;
@@ -374,18 +368,12 @@ extern "C" int fem_solve_noalloc(fem_ctx* ctx, const fem_solve_opts* opts, const
               (long long)c.ndofs, (long long)kNoAllocMaxDofs);
     return FEM_EINVAL;
   }
-  int dev = -1;
-  TETMF_CK(cudaGetDevice(&dev));
-  if (dev != c.device) {
-    set_error("fem_solve_noalloc: current device %d is not the context's device %d", dev, c.device);
-    return FEM_EINVAL;
-  }
   void* base = nullptr;
-  if (int e = noalloc_address(dev, &base)) return e;
+  if (int e = noalloc_address(c, &base)) return e;
   carve(static_cast<uint8_t*>(base), c.ndofs, w);
   // the reduction ticket must start at zero; every other array is written before it is read
   TETMF_CK(cudaMemsetAsync(w.ticket, 0, 64, as_stream(stream)));
   static thread_local double host_scal[S_COUNT];
   w.host_scal = host_scal;
-  return solve_with(c, w, opts, b, x, stats, stream);
+  return solve_with("fem_solve_noalloc", c, w, opts, b, x, stats, stream);
 }

@@ -323,3 +323,13 @@ class FemApply(torch.autograd.Function):
 
 def fem_apply(space: FemSpace, u, k=None, prec="fp64"):
     return FemApply.apply(space, u, k, prec)
+
+
+def fma_probe(kind: str, iters: int, sink, stream=None):
+    """Launch the library's arithmetic-throughput probe (fem_fma_probe) on the current device:
+    kind "fp64", "fp32" or "fp32x2"; sink is a device tensor of at least one float64.  Returns the
+    floating-point operations launched; time the call with events on `stream`."""
+    flops = ctypes.c_double()
+    call("fem_fma_probe", {"fp64": 0, "fp32": 1, "fp32x2": 2}[kind], int(iters), _ptr(sink), ctypes.byref(flops),
+         _stream(stream))
+    return flops.value

@@ -30,3 +30,46 @@ def test_null_arguments_rejected():
     assert b"null" in L.fem_last_error()
     assert L.fem_apply(None, 0, None, None, None, None) == _lib.FEM_EINVAL
     assert L.fem_destroy(None) == _lib.FEM_OK
+
+
+def test_device_calls_refused_on_a_host_only_context():
+    """A host-only context (device = -1) refuses every device call with FEM_EINVAL before any CUDA
+    call is made (this runs without a GPU)."""
+    import numpy as np
+
+    import synth
+    from paper_2509_10226_gb300.fem import FemSpace
+
+    xyz, cells = synth.kuhn_cube(2)
+    sp = FemSpace(xyz, cells, degree=1, device=-1)
+    L = _lib.lib()
+    assert L.fem_apply(sp._h, _lib.FEM_FP32, None, None, None, None) == _lib.FEM_EINVAL
+    assert b"host-only" in L.fem_last_error()
+    st = _lib.SolveStats()
+    opts = _lib.SolveOpts(_lib.FEM_SOLVE_FP64_PCG, _lib.FEM_FP32, 1e-10, 1e-3, 5, 5)
+    assert L.fem_solve_noalloc(sp._h, ctypes.byref(opts), None, None, ctypes.byref(st), None) == _lib.FEM_EINVAL
+    assert b"host-only" in L.fem_last_error()
+    assert np.isfinite(sp.n_dofs)
+
+
+@pytest.mark.gpu
+def test_device_mismatch_refused_before_launch():
+    """Device calls need the calling thread's current device to be the context's device; with another
+    device current they return FEM_EINVAL and launch nothing.  Needs two visible GPUs."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available() or torch.cuda.device_count() < 2:
+        pytest.skip("needs two CUDA devices")
+    import synth
+    from paper_2509_10226_gb300.fem import FemSpace
+
+    xyz, cells = synth.kuhn_cube(2)
+    sp = FemSpace(xyz, cells, degree=1, device=0)
+    u = torch.zeros(sp.n_dofs, device="cuda:0")
+    y = torch.full((sp.n_dofs,), 7.0, device="cuda:0")
+    L = _lib.lib()
+    with torch.cuda.device(1):
+        s = L.fem_apply(sp._h, _lib.FEM_FP32, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(y.data_ptr()), None,
+                        None)
+        assert s == _lib.FEM_EINVAL and b"current device 1" in L.fem_last_error()
+    torch.cuda.synchronize(0)
+    assert bool((y == 7.0).all())

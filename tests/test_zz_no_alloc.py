@@ -59,6 +59,44 @@ def test_noalloc_matches_fem_solve_twice(space, mode, inner):
         assert st[1] <= 2 * st_ref[1] + 16 and st_ref[1] <= 2 * st[1] + 16
 
 
+def test_noalloc_allocates_no_device_memory():
+    """A fresh context of 185,193 DoFs (fem_solve would allocate about 12 MB of work vectors for
+    it): after a first call (which loads the library's device code and looks the work array up),
+    two more fem_solve_noalloc calls leave the device's free memory unchanged, while one fem_solve
+    call on the same context visibly takes its work space."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_10226_gb300 import _lib
+    from paper_2509_10226_gb300.fem import FemSpace
+
+    xyz, cells = synth.kuhn_cube(28, jitter=0.2, seed=0)
+    sp = FemSpace(xyz, cells, degree=2, dirichlet=True, device=0)  # 57^3 = 185,193 DoFs
+    assert 150_000 < sp.n_dofs <= _lib.FEM_SOLVE_NOALLOC_MAX_DOFS
+    b = sp.rhs_const(1.0)
+    x = torch.zeros_like(b)
+    opts = _lib.SolveOpts(_lib.FEM_SOLVE_IR_MIXED, _lib.FEM_TF32, 1e-10, 1e-3, 50, 20000)
+    st = _lib.SolveStats()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call(name):
+        x.zero_()
+        status = getattr(_lib.lib(), name)(sp._h, ctypes.byref(opts), ctypes.c_void_p(b.data_ptr()),
+                                           ctypes.c_void_p(x.data_ptr()), ctypes.byref(st), stream)
+        _lib.check(status, name)
+        torch.cuda.synchronize()
+        assert st.rel_residual <= RTOL
+
+    call("fem_solve_noalloc")
+    free0 = torch.cuda.mem_get_info()[0]
+    call("fem_solve_noalloc")
+    call("fem_solve_noalloc")
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, f"fem_solve_noalloc changed free device memory by {free0 - free1} bytes"
+    call("fem_solve")
+    free2 = torch.cuda.mem_get_info()[0]
+    assert free1 - free2 >= 8 << 20, "fem_solve's work space should be visible to this check"
+
+
 def test_noalloc_rejects_oversize():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
