@@ -33,7 +33,9 @@
  *     are constrained; the operator is P A P + (I - P) (identity rows).
  *
  * Numbering.  The library renumbers cells (Morton order of centroids unless
- * reorder = FEM_REORDER_NONE) and DoFs (first touch in cell order).  Vectors
+ * reorder = FEM_REORDER_NONE) and DoFs (grouped by the set of 128-cell
+ * batches of the library cell order that touch them, batches in order; within a
+ * group, first touch in cell order).  Vectors
  * passed to the hot calls are in library order; fem_dof_permutation and
  * fem_cell_permutation translate.  Coefficients k and dk are [n_cells][nq]
  * row-major in library cell order.

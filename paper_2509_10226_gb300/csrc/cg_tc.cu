@@ -15,13 +15,14 @@
 // consistent (constants map to zero, operand error relative to the gradient).
 //
 // Data movement: each 128-cell tile carries the sorted list of the distinct
-// unconstrained DoFs its cells touch and, per (cell, local node), a 16-bit
-// index into that list.  The tile's values are gathered once per distinct DoF
-// (cp.async, mostly contiguous addresses thanks to the Morton/first-touch
-// numbering), and the tile's contributions are pre-reduced in shared memory
-// before one global atomic per distinct DoF: about 3x fewer L2 atomics and
-// gather requests than one per (cell, node) (the masked gather and the
-// scatter of Sec. 2.4).
+// 16-byte groups (4 consecutive DoFs) that hold its unconstrained DoFs and, per
+// (cell, local node), a 16-bit position in the tile's staging.  Set-up numbers
+// the DoFs by the set of tiles sharing them, so a tile's DoFs fill its groups
+// densely (at P3 about 880 DoFs in 240 groups).  The values are gathered with
+// one 16-byte cp.async per group, and the tile's contributions are pre-reduced
+// in shared memory before one 16-byte vector atomic per group: about 11x fewer
+// gather requests and L2 atomics than one per (cell, node) (the masked gather
+// and the scatter of Sec. 2.4).
 //
 // A warpgroup of 128 threads owns one TMEM lane per cell and loops over tiles:
 //   1. build row m of U' from the staged values, write it to shared memory;
@@ -69,17 +70,19 @@ constexpr int kT = kTile;
 // of t+2 in flight, tile t-1 being flushed and then the metadata of t+3) where TMEM keeps a CTA below
 // four warpgroups, so that shared memory is left over; three (tile t, values of t+1 in flight, tile
 // t-1 and then the metadata of t+2) where four warpgroups fit, which need the shared memory.
+// lmax: the longest group list, a multiple of 4
 template <int ND, int NQ, bool HAS_K>
 struct Stage {
-  uint32_t* lidx;   // [NDP / 2][128] pairs of 16-bit list positions (node 2w low, 2w+1 high)
-  int32_t* list;    // [lmax] distinct DoFs of the tile
-  float* vals;      // [lmax] their values, then the tile's pre-reduced results
+  uint32_t* lidx;   // [NDP / 2][128] pairs of 16-bit staging positions (node 2w low, 2w+1 high)
+  int32_t* list;    // [lmax] distinct 16-byte groups of the tile
+  float* vals;      // [4 lmax + 4] their values and the zero slot, then the tile's pre-reduced results
   float* kt;        // [128][NQ | 1] coefficient tile (HAS_K)
 };
 
 template <int ND, int NQ, bool HAS_K>
 __host__ __device__ constexpr size_t stage_bytes(int lmax) {
-  return size_t(round_up(ND, 2)) * kT * 2 + size_t(round_up(lmax, 4)) * 8 + (HAS_K ? size_t(kT) * (NQ | 1) * 4 : 0);
+  return size_t(round_up(ND, 2)) * kT * 2 + size_t(lmax) * 4 + (size_t(lmax) * 4 + 4) * 4 +
+         (HAS_K ? size_t(kT) * (NQ | 1) * 4 : 0);
 }
 
 template <int ND, int NQ, bool HAS_K>
@@ -88,24 +91,44 @@ __device__ inline Stage<ND, NQ, HAS_K> stage_at(uint8_t* p, int lmax) {
   st.lidx = reinterpret_cast<uint32_t*>(p);
   p += round_up(ND, 2) * kT * 2;
   st.list = reinterpret_cast<int32_t*>(p);
-  p += round_up(lmax, 4) * 4;
+  p += size_t(lmax) * 4;
   st.vals = reinterpret_cast<float*>(p);
-  p += round_up(lmax, 4) * 4;
+  p += (size_t(lmax) * 4 + 4) * 4;
   st.kt = HAS_K ? reinterpret_cast<float*>(p) : nullptr;
   return st;
 }
 
-// copy a tile's list and node positions (and coefficients) into a stage; m = thread of the warpgroup
+// where a tile's group list starts and how long it is; loaded a tile ahead of its use, so that the
+// copies below do not wait on the load
+struct Span {
+  int64_t o;
+  int L;
+};
+__device__ inline Span load_span(const int64_t* __restrict__ tl_span, int64_t tile, int64_t ntiles) {
+  if (tile >= ntiles) return Span{0, 0};
+  return Span{__ldg(tl_span + 2 * tile), int(__ldg(tl_span + 2 * tile + 1))};
+}
+// the cell metric of row m of a tile (6 values), likewise loaded a tile ahead
+struct Metric {
+  float v[6];
+};
+__device__ inline Metric load_metric(const float* __restrict__ metric, int64_t tile, int64_t ntiles, int m) {
+  Metric r;
+  const float* mp = metric + (tile < ntiles ? tile : 0) * 6 * kT + m;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) r.v[a] = __ldg(mp + a * kT);
+  return r;
+}
+
+// the copies of a tile's list and node positions (and coefficients) into a stage; m = thread of the
+// warpgroup
 template <int ND, int NQ, bool HAS_K>
-__device__ inline int issue_meta(const Stage<ND, NQ, HAS_K>& st, int m, int64_t tile,
-                                     const int64_t* __restrict__ tl_span, const int32_t* __restrict__ tl_list,
-                                     const uint16_t* __restrict__ tl_lidx, const float* __restrict__ kcoef,
-                                     int64_t nc) {
+__device__ inline void meta_copies(const Stage<ND, NQ, HAS_K>& st, int m, int64_t tile, Span sp,
+                                   const int32_t* __restrict__ tl_list, const uint16_t* __restrict__ tl_lidx,
+                                   const float* __restrict__ kcoef, int64_t nc) {
   constexpr int NDP = round_up(ND, 2);
-  const int64_t o0 = tl_span[2 * tile];
-  const int L = int(tl_span[2 * tile + 1]);
-  const int32_t* src_list = tl_list + o0;  // 16-byte aligned, padded to a multiple of 4 entries
-  for (int i = m; i < (L + 3) / 4; i += kT) cp_async16(st.list + 4 * i, src_list + 4 * i);
+  const int32_t* src_list = tl_list + sp.o;  // 16-byte aligned, padded to a multiple of 4 entries
+  for (int i = m; i < (sp.L + 3) / 4; i += kT) cp_async16(st.list + 4 * i, src_list + 4 * i);
   const uint8_t* li = reinterpret_cast<const uint8_t*>(tl_lidx + tile * NDP * kT);
   for (int i = m; i < NDP * kT * 2 / 16; i += kT) cp_async16(reinterpret_cast<uint8_t*>(st.lidx) + 16 * i, li + 16 * i);
   if constexpr (HAS_K) {
@@ -114,16 +137,51 @@ __device__ inline int issue_meta(const Stage<ND, NQ, HAS_K>& st, int m, int64_t 
     const float* src = kcoef + cell0 * NQ;
     for (int i = m; i < int(n); i += kT) cp_async4(st.kt + (i / NQ) * (NQ | 1) + i % NQ, src + i);
   }
-  cp_async_commit();
-  return L;
 }
 
-// gather the values of a tile's distinct DoFs (after its list has arrived)
+// copy a tile's list and node positions (and coefficients) into a stage, as one cp.async group
 template <int ND, int NQ, bool HAS_K>
-__device__ inline void issue_gather(const Stage<ND, NQ, HAS_K>& st, int m, int L, const float* __restrict__ u) {
-  for (int i = m; i < L; i += kT) cp_async4(st.vals + i, u + st.list[i]);
-  if (m == 0) st.vals[L] = 0.0f;  // slot of constrained / padding nodes
+__device__ inline int issue_meta(const Stage<ND, NQ, HAS_K>& st, int m, int64_t tile, Span sp,
+                                     const int32_t* __restrict__ tl_list,
+                                     const uint16_t* __restrict__ tl_lidx, const float* __restrict__ kcoef,
+                                     int64_t nc) {
+  meta_copies<ND, NQ, HAS_K>(st, m, tile, sp, tl_list, tl_lidx, kcoef, nc);
   cp_async_commit();
+  return sp.L;
+}
+
+// gather the values of a tile's groups (after its list has arrived) as one cp.async group: one
+// 16-byte copy per group where u is 16-byte aligned and the group lies inside the vector (n DoFs),
+// else the group's DoFs one by one (the vector's last, partial group)
+template <int ND, int NQ, bool HAS_K>
+__device__ inline void issue_gather(const Stage<ND, NQ, HAS_K>& st, int m, int L, const float* __restrict__ u,
+                                    int64_t n, bool u16) {
+  for (int i = m; i < L; i += kT) {
+    const int64_t base = 4 * int64_t(st.list[i]);
+    if (u16 && base + 4 <= n) {
+      cp_async16(st.vals + 4 * i, u + base);
+    } else {
+      for (int e = 0; e < 4; ++e)
+        if (base + e < n) cp_async4(st.vals + 4 * i + e, u + base + e);
+    }
+  }
+  if (m == 0) *reinterpret_cast<float4*>(st.vals + 4 * L) = make_float4(0.f, 0.f, 0.f, 0.f);  // zero slot
+  cp_async_commit();
+}
+
+// add a tile's pre-reduced groups to y: one 16-byte vector reduction (no return value) per group
+// where y is 16-byte aligned and the group lies inside the vector, else one atomic per DoF
+__device__ inline void flush_group(float* __restrict__ y, int32_t group, float4 v, int64_t n, bool y16) {
+  const int64_t base = 4 * int64_t(group);
+  if (y16 && base + 4 <= n) {
+    // no memory clobber: the loads of later groups may be scheduled before it (nothing here reads y)
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(y + base), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w));
+  } else {
+    const float w[4] = {v.x, v.y, v.z, v.w};
+    for (int e = 0; e < 4; ++e)
+      if (base + e < n) atomicAdd(y + base + e, w[e]);
+  }
 }
 
 
@@ -155,7 +213,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3, CURVED>()
                   const uint16_t* __restrict__ tl_lidx, const float* __restrict__ metric,
                   const uint8_t* __restrict__ bimg, const float* __restrict__ u, float* __restrict__ y,
                   const float* __restrict__ kcoef, int64_t nc, int64_t ntiles, int lmax, uint32_t tmem_cols,
-                  int32_t* __restrict__ status, const float* __restrict__ qmetric) {
+                  int32_t* __restrict__ status, const float* __restrict__ qmetric, int64_t ndofs, int aligned) {
   using S = TcShape<ND, NQ, BF16>;
   using St = Stage<ND, NQ, HAS_K>;
   static_assert(!(X3 && BF16), "3xTF32 splits TF32 operands");
@@ -170,6 +228,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3, CURVED>()
   const int g = threadIdx.x / kT;   // warpgroup
   const int m = threadIdx.x % kT;   // row of the tile = TMEM lane
   const int warp = threadIdx.x >> 5;
+  const bool u16 = aligned & 1, y16 = aligned & 2;  // u, y 16-byte aligned
   uint8_t* sB1 = smem;                        // [B1 | B2] high parts, then [B1 | B2] low parts (X3)
   uint8_t* sB2 = sB1 + S::B1_BYTES;
   uint8_t* sA1 = smem + NIMG * IMG_BYTES + size_t(g) * NIMG * S::A1_BYTES;
@@ -203,7 +262,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3, CURVED>()
   int64_t tile = int64_t(blockIdx.x) * G + g;
   int L_cur = 0, L_next = 0, L_next2 = 0;
   if (tile < ntiles)
-    L_cur = issue_meta<ND, NQ, HAS_K>(stage(0), m, tile, tl_span, tl_list, tl_lidx, kcoef, nc);
+    L_cur = issue_meta<ND, NQ, HAS_K>(stage(0), m, tile, load_span(tl_span, tile, ntiles), tl_list, tl_lidx, kcoef, nc);
   else
     cp_async_commit();
   cp_async_wait_group<0>();
@@ -214,19 +273,19 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3, CURVED>()
   const uint32_t tmem = *tslot + uint32_t(g * TCOLS);
   const uint32_t lane_base = tmem + (uint32_t((warp & 3) * 32) << 16);
   const uint32_t aA1 = smem_u32(sA1), aB1 = smem_u32(sB1), aB2 = smem_u32(sB2);
-  if (tile < ntiles) issue_gather<ND, NQ, HAS_K>(stage(0), m, L_cur, u);
+  if (tile < ntiles) issue_gather<ND, NQ, HAS_K>(stage(0), m, L_cur, u, ndofs, u16);
   else cp_async_commit();
   if (tile + stride < ntiles)
-    L_next = issue_meta<ND, NQ, HAS_K>(stage(1), m, tile + stride, tl_span, tl_list, tl_lidx, kcoef, nc);
+    L_next = issue_meta<ND, NQ, HAS_K>(stage(1), m, tile + stride, load_span(tl_span, tile + stride, ntiles), tl_list, tl_lidx, kcoef, nc);
   else
     cp_async_commit();
   if constexpr (D == 2) {
     cp_async_wait_group<0>();
     wg_sync(g);
-    if (tile + stride < ntiles) issue_gather<ND, NQ, HAS_K>(stage(1), m, L_next, u);
+    if (tile + stride < ntiles) issue_gather<ND, NQ, HAS_K>(stage(1), m, L_next, u, ndofs, u16);
     else cp_async_commit();
     if (tile + 2 * stride < ntiles)
-      L_next2 = issue_meta<ND, NQ, HAS_K>(stage(2), m, tile + 2 * stride, tl_span, tl_list, tl_lidx, kcoef, nc);
+      L_next2 = issue_meta<ND, NQ, HAS_K>(stage(2), m, tile + 2 * stride, load_span(tl_span, tile + 2 * stride, ntiles), tl_list, tl_lidx, kcoef, nc);
     else
       cp_async_commit();
   } else {
@@ -282,27 +341,38 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3, CURVED>()
       for (int j = 0; j < ND; ++j) atomicAdd(iv + pos(j), __float2int_rn(yv[j] * scale));
       wg_sync(g);
       const float inv = __int_as_float((127 - 24 + E) << 23);
-      for (int i = m; i < Ls; i += kT) atomicAdd(y + st.list[i], float(iv[i]) * inv);
+      const int4* i4 = reinterpret_cast<const int4*>(iv);
+      for (int i = m; i < Ls; i += kT) {
+        const int4 a = i4[i];
+        flush_group(y, st.list[i], make_float4(float(a.x) * inv, float(a.y) * inv, float(a.z) * inv, float(a.w) * inv),
+                    ndofs, y16);
+      }
     } else {
 #pragma unroll
       for (int j = 0; j < ND; ++j) atomicAdd(st.vals + pos(j), yv[j]);
       wg_sync(g);
-      for (int i = m; i < Ls; i += kT) atomicAdd(y + st.list[i], st.vals[i]);
+      for (int i = m; i < Ls; i += kT)
+        flush_group(y, st.list[i], reinterpret_cast<const float4*>(st.vals)[i], ndofs, y16);
     }
   };
 
+  // the span of the tile whose metadata is copied next, and (affine cells) the metric of the
+  // current tile, both loaded one tile ahead
+  Span sp_next = load_span(tl_span, tile + (D + 1) * stride, ntiles);
+  Metric met_next;
+  if constexpr (!CURVED) met_next = load_metric(metric, tile, ntiles, m);
   for (; tile < ntiles; tile += stride, b = (b + 1 == kStages ? 0 : b + 1)) {
     const int bg = (b + D) % kStages;      // tile t+D: gather target
     const int bm = (b + D + 1) % kStages;  // tile t-1 (flushed), then the metadata of t+D+1
     const St cur = stage(b);
     const int64_t tg = tile + D * stride, tm = tile + (D + 1) * stride;
-    // this cell's metric, consumed after GEMM 1 (coalesced loads, latency hidden by the row build);
-    // curved cells read one metric per point during the metric step instead
+    // this cell's metric, consumed after GEMM 1; curved cells read one metric per point during the
+    // metric step instead
     float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, m5 = 0.f;
     if constexpr (!CURVED) {
-      const float* mp = metric + tile * 6 * kT + m;
-      m0 = __ldg(mp), m1 = __ldg(mp + kT), m2 = __ldg(mp + 2 * kT), m3 = __ldg(mp + 3 * kT), m4 = __ldg(mp + 4 * kT),
-      m5 = __ldg(mp + 5 * kT);
+      m0 = met_next.v[0], m1 = met_next.v[1], m2 = met_next.v[2], m3 = met_next.v[3], m4 = met_next.v[4],
+      m5 = met_next.v[5];
+      met_next = load_metric(metric, tile + stride, ntiles, m);
     }
     const int L = L_cur;
     int L_new = 0;
@@ -356,7 +426,7 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3, CURVED>()
       }
       mma_commit(bar_a);
     }
-    for (int i = m; i < (L + 4) / 4; i += kT) reinterpret_cast<float4*>(cur.vals)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = m; i < L + 1; i += kT) reinterpret_cast<float4*>(cur.vals)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (have_prev) scatter(stage(bm), L_prev, lw_prev);
     cp_async_wait_group<0>();  // this thread's share of the metadata of t+D (and, D = 2, values of t+1)
     // one thread waits for GEMM 1; the barrier also publishes the copies awaited above and the end of
@@ -367,12 +437,13 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3, CURVED>()
     if (failed) break;
     tc_fence_after();
     // gather of tile t+D, metadata of tile t+D+1
-    if (tg < ntiles) issue_gather<ND, NQ, HAS_K>(stage(bg), m, D == 2 ? L_next2 : L_next, u);
+    if (tg < ntiles) issue_gather<ND, NQ, HAS_K>(stage(bg), m, D == 2 ? L_next2 : L_next, u, ndofs, u16);
     else cp_async_commit();
     if (tm < ntiles)
-      L_new = issue_meta<ND, NQ, HAS_K>(stage(bm), m, tm, tl_span, tl_list, tl_lidx, kcoef, nc);
+      L_new = issue_meta<ND, NQ, HAS_K>(stage(bm), m, tm, sp_next, tl_list, tl_lidx, kcoef, nc);
     else
       cp_async_commit();
+    sp_next = load_span(tl_span, tm + stride, ntiles);
     // 3. D_e per quadrature point: G in TMEM becomes Q = (k_q) M_e g_q (w_q is folded into the table of GEMM 2)
     metric_to_q<ND, NQ, BF16, HAS_K, X3, CURVED>(lane_base, m0, m1, m2, m3, m4, m5, HAS_K ? cur.kt + m * KS : nullptr,
                                                  QLO, CURVED ? qmetric + tile * NQ * 6 * kT + m : nullptr);
@@ -432,10 +503,10 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3, CURVED>()
 // warpgroup that takes every finished tile off their hands: it reads Y' straight from the compute
 // warpgroup's TMEM columns, pre-reduces it into that tile's stage and adds the distinct values to
 // y, so the scatter no longer sits on the compute warpgroups' critical path.  Per compute
-// warpgroup five mbarriers order the hand-offs, each completing once per tile:
+// warpgroup four mbarriers order the hand-offs, each completing once per tile:
 //   g1: GEMM 1 done (compute);  g2: GEMM 2 done (compute, scatter);  rdy: tile's stage ready for
 //   the scatter;  yfree: Y' read by the scatter (GEMM 2 of the next tile may overwrite it);
-//   stfree: the tile's stage flushed (it may be refilled).
+//   and a counter of the warpgroup's flushed tiles (their stages may be refilled).
 // The scatter warpgroup visits tiles in the compute warpgroups' round-robin order; every signal is
 // awaited before the next phase of the same barrier can complete, so parities never run two
 // phases ahead.  Waits are bounded (about 1 s) and share an abort flag: once one gives up, every
@@ -446,12 +517,17 @@ constexpr int ws_groups() {
   return tc_max_groups<ND, NQ, BF16, false, false>();
 }
 
+// Four stages per compute warpgroup: during tile k the values of tile k+2 are gathered and the
+// metadata of tile k+3 is copied into the stage of tile k-1 once the scatter has flushed it.  That
+// release is a count of flushed tiles (released and acquired in shared memory), which stays valid
+// however far the scatter runs ahead.
 template <int ND, int NQ, bool BF16>
 __global__ void __launch_bounds__(kT * (ws_groups<ND, NQ, BF16>() + 1), 1)
     k_cg_apply_tc_ws(const int64_t* __restrict__ tl_span, const int32_t* __restrict__ tl_list,
                      const uint16_t* __restrict__ tl_lidx, const float* __restrict__ metric,
                      const uint8_t* __restrict__ bimg, const float* __restrict__ u, float* __restrict__ y,
-                     int64_t nc, int64_t ntiles, int lmax, uint32_t tmem_cols, int32_t* __restrict__ status) {
+                     int64_t nc, int64_t ntiles, int lmax, uint32_t tmem_cols, int32_t* __restrict__ status,
+                     int64_t ndofs, int aligned) {
   using S = TcShape<ND, NQ, BF16>;
   using St = Stage<ND, NQ, false>;
   constexpr int NDP = round_up(ND, 2);
@@ -459,14 +535,18 @@ __global__ void __launch_bounds__(kT * (ws_groups<ND, NQ, BF16>() + 1), 1)
   constexpr int kStages = 4;
   constexpr int IMG_BYTES = S::B1_BYTES + S::B2_BYTES;
   extern __shared__ __align__(1024) uint8_t smem[];
-  const int G = blockDim.x / kT - 1;  // compute warpgroups; warpgroup G scatters
-  const int g = threadIdx.x / kT;
+  const int G = blockDim.x / kT - 1;  // compute warpgroups
+  // roles: the scatter warpgroup is hardware warpgroup 0 (the lowest warp numbers, which the warp
+  // schedulers favour: the scatter serves every tile and sets the pace), compute warpgroups
+  // 0..G-1 are hardware warpgroups 1..G; g is the role index (G = scatter)
+  const int g = threadIdx.x < kT ? G : int(threadIdx.x / kT) - 1;
   const int m = threadIdx.x % kT;
   const int warp = threadIdx.x >> 5;
+  const bool u16 = aligned & 1, y16 = aligned & 2;  // u, y 16-byte aligned
   uint8_t* sB1 = smem;
   uint8_t* sB2 = sB1 + S::B1_BYTES;
   uint8_t* misc = smem + IMG_BYTES + size_t(G) * S::A1_BYTES;  // [G][64] barriers, then TMEM slot, abort, maxima
-  auto bars = [&](int gg) { return smem_u32(misc + 64 * gg); };  // g1, g2, rdy, yfree, stfree (8 bytes each)
+  auto bars = [&](int gg) { return smem_u32(misc + 64 * gg); };  // g1, g2, rdy, yfree, flushed (8 bytes each)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 64 * G);
   volatile int* abort = reinterpret_cast<volatile int*>(misc + 64 * G + 4);
   uint32_t* wmax = reinterpret_cast<uint32_t*>(misc + 64 * G + 16);
@@ -480,8 +560,10 @@ __global__ void __launch_bounds__(kT * (ws_groups<ND, NQ, BF16>() + 1), 1)
     uint4* dst = reinterpret_cast<uint4*>(sB1);
     for (int i = threadIdx.x; i < IMG_BYTES / 16; i += blockDim.x) dst[i] = src[i];
   }
-  if (g < G && m == 0)
-    for (int k = 0; k < 5; ++k) mbar_init(bars(g) + 8 * k);
+  if (g < G && m == 0) {
+    for (int k = 0; k < 4; ++k) mbar_init(bars(g) + 8 * k);
+    st_release_u32(bars(g) + 32, 0u);  // flushed tiles of this compute warpgroup
+  }
   if (threadIdx.x == 0) *abort = 0;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -496,11 +578,11 @@ __global__ void __launch_bounds__(kT * (ws_groups<ND, NQ, BF16>() + 1), 1)
     uint8_t* sA1 = smem + IMG_BYTES + size_t(g) * S::A1_BYTES;
     auto stage = [&](int i) { return stage_of(g, i); };
     const uint32_t b_g1 = bars(g), b_g2 = bars(g) + 8, b_rdy = bars(g) + 16, b_yfree = bars(g) + 24,
-                   b_stfree = bars(g) + 32;
+                   b_flushed = bars(g) + 32;
     int64_t tile = int64_t(blockIdx.x) * G + g;
     int L_cur = 0, L_next = 0, L_next2 = 0;
     if (tile < ntiles)
-      L_cur = issue_meta<ND, NQ, false>(stage(0), m, tile, tl_span, tl_list, tl_lidx, nullptr, nc);
+      L_cur = issue_meta<ND, NQ, false>(stage(0), m, tile, load_span(tl_span, tile, ntiles), tl_list, tl_lidx, nullptr, nc);
     else
       cp_async_commit();
     cp_async_wait_group<0>();
@@ -511,28 +593,32 @@ __global__ void __launch_bounds__(kT * (ws_groups<ND, NQ, BF16>() + 1), 1)
     const uint32_t tmem = *tslot + uint32_t(g * TCOLS);
     const uint32_t lane_base = tmem + (uint32_t((warp & 3) * 32) << 16);
     const uint32_t aA1 = smem_u32(sA1), aB1 = smem_u32(sB1), aB2 = smem_u32(sB2);
-    if (tile < ntiles) issue_gather<ND, NQ, false>(stage(0), m, L_cur, u);
+    if (tile < ntiles) issue_gather<ND, NQ, false>(stage(0), m, L_cur, u, ndofs, u16);
     else cp_async_commit();
     if (tile + stride < ntiles)
-      L_next = issue_meta<ND, NQ, false>(stage(1), m, tile + stride, tl_span, tl_list, tl_lidx, nullptr, nc);
+      L_next = issue_meta<ND, NQ, false>(stage(1), m, tile + stride, load_span(tl_span, tile + stride, ntiles), tl_list, tl_lidx, nullptr, nc);
     else
       cp_async_commit();
     cp_async_wait_group<0>();
     wg_sync(g);
-    if (tile + stride < ntiles) issue_gather<ND, NQ, false>(stage(1), m, L_next, u);
+    if (tile + stride < ntiles) issue_gather<ND, NQ, false>(stage(1), m, L_next, u, ndofs, u16);
     else cp_async_commit();
     if (tile + 2 * stride < ntiles)
-      L_next2 = issue_meta<ND, NQ, false>(stage(2), m, tile + 2 * stride, tl_span, tl_list, tl_lidx, nullptr, nc);
+      L_next2 = issue_meta<ND, NQ, false>(stage(2), m, tile + 2 * stride, load_span(tl_span, tile + 2 * stride, ntiles), tl_list, tl_lidx, nullptr, nc);
     else
       cp_async_commit();
     int b = 0;
+    // the span of the tile whose metadata is copied next and the metric of the current tile, both
+    // loaded one tile ahead
+    Span sp_next = load_span(tl_span, tile + 3 * stride, ntiles);
+    Metric met_next = load_metric(metric, tile, ntiles, m);
     for (uint32_t k = 0; tile < ntiles; tile += stride, ++k, b = (b + 1 == kStages ? 0 : b + 1)) {
-      const int bg = (b + 2) % kStages, bm = (b + 3) % kStages;
+      const int bg = (b + 2) % kStages, bm = (b + 3) % kStages;  // bm: held tile k + 3 - kStages
       const St cur = stage(b);
       const int64_t tg = tile + 2 * stride, tm = tile + 3 * stride;
-      const float* mp = metric + tile * 6 * kT + m;
-      const float m0 = __ldg(mp), m1 = __ldg(mp + kT), m2 = __ldg(mp + 2 * kT), m3 = __ldg(mp + 3 * kT),
-                  m4 = __ldg(mp + 4 * kT), m5 = __ldg(mp + 5 * kT);
+      const float m0 = met_next.v[0], m1 = met_next.v[1], m2 = met_next.v[2], m3 = met_next.v[3],
+                  m4 = met_next.v[4], m5 = met_next.v[5];
+      met_next = load_metric(metric, tile + stride, ntiles, m);
       const int L = L_cur;
       int L_new = 0;
       // rows of U' (difference form)
@@ -564,21 +650,21 @@ __global__ void __launch_bounds__(kT * (ws_groups<ND, NQ, BF16>() + 1), 1)
         mma_commit(b_g1);
       }
       // the tile's accumulator (its values were read into the rows above)
-      for (int i = m; i < (L + 4) / 4; i += kT)
-        reinterpret_cast<float4*>(cur.vals)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = m; i < L + 1; i += kT) reinterpret_cast<float4*>(cur.vals)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       cp_async_wait_group<0>();  // values of t+1, metadata of t+2 (this thread's share)
       if (m == 0) failed |= !mbar_wait_ab(b_g1, k & 1, abort);
       failed = wg_any(g, failed);
       if (failed) break;
       tc_fence_after();
       // gather of t+2; metadata of t+3 into the stage of t-1 once the scatter has flushed it
-      if (tg < ntiles) issue_gather<ND, NQ, false>(stage(bg), m, L_next2, u);
+      if (tg < ntiles) issue_gather<ND, NQ, false>(stage(bg), m, L_next2, u, ndofs, u16);
       else cp_async_commit();
-      if (k > 0) failed |= !mbar_wait_ab(b_stfree, (k - 1) & 1, abort);
+      if (k + 3 >= kStages) failed |= !count_wait_ab(b_flushed, k + 4 - kStages, abort);
       if (tm < ntiles)
-        L_new = issue_meta<ND, NQ, false>(stage(bm), m, tm, tl_span, tl_list, tl_lidx, nullptr, nc);
+        L_new = issue_meta<ND, NQ, false>(stage(bm), m, tm, sp_next, tl_list, tl_lidx, nullptr, nc);
       else
         cp_async_commit();
+      sp_next = load_span(tl_span, tm + stride, ntiles);
       // TF32 keeps one chunk live at a time (the warp-specialised kernel runs at 128 registers)
       metric_to_q<ND, NQ, BF16, false, false, false, !BF16>(lane_base, m0, m1, m2, m3, m4, m5, nullptr);
       tmem_wait_st();
@@ -654,15 +740,29 @@ __global__ void __launch_bounds__(kT * (ws_groups<ND, NQ, BF16>() + 1), 1)
           for (int j = 0; j < ND; ++j) atomicAdd(iv + pos(j), __float2int_rn(yv[j] * scale));
           wg_sync(G);
           const float inv = __int_as_float((127 - 24 + E) << 23);
-          for (int i = m; i < Ls; i += kT) atomicAdd(y + st.list[i], float(iv[i]) * inv);
+          const int4* i4 = reinterpret_cast<const int4*>(iv);
+          // two groups per thread and round, both loaded before either is added
+          for (int i = m; i < Ls; i += 2 * kT) {
+            const bool two = i + kT < Ls;
+            const int4 a = i4[i];
+            const int32_t ga = st.list[i];
+            const int4 c = two ? i4[i + kT] : make_int4(0, 0, 0, 0);
+            const int32_t gc = two ? st.list[i + kT] : 0;
+            flush_group(y, ga, make_float4(float(a.x) * inv, float(a.y) * inv, float(a.z) * inv, float(a.w) * inv),
+                        ndofs, y16);
+            if (two)
+              flush_group(y, gc, make_float4(float(c.x) * inv, float(c.y) * inv, float(c.z) * inv, float(c.w) * inv),
+                          ndofs, y16);
+          }
         } else {
 #pragma unroll
           for (int j = 0; j < ND; ++j) atomicAdd(st.vals + pos(j), yv[j]);
           wg_sync(G);
-          for (int i = m; i < Ls; i += kT) atomicAdd(y + st.list[i], st.vals[i]);
+          for (int i = m; i < Ls; i += kT)
+            flush_group(y, st.list[i], reinterpret_cast<const float4*>(st.vals)[i], ndofs, y16);
         }
         wg_sync(G);  // the flush of this stage is complete (and wmax may be reused)
-        if (m == 0) mbar_arrive(bb + 32);
+        if (m == 0) st_release_u32(bb + 32, k + 1);  // tiles 0..k of this warpgroup are flushed
       }
     }
   }
@@ -736,10 +836,15 @@ int prepare(Ctx& c) {
   return upload_image<ND, NQ, true, false>(c, &c.d_tc_bf16);
 }
 
+// bit 0: u is 16-byte aligned, bit 1: y is (the kernels then move whole groups of 4 values)
+int alignment_flags(const float* u, const float* y) {
+  return ((reinterpret_cast<uintptr_t>(u) & 15) == 0 ? 1 : 0) | ((reinterpret_cast<uintptr_t>(y) & 15) == 0 ? 2 : 0);
+}
+
 template <int ND, int NQ, bool BF16, bool HAS_K, bool X3, bool CURVED>
 int launch_g(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) {
   constexpr int TCOLS = tc_tcols<ND, NQ, BF16, X3>();
-  const int lmax = round_up(c.tl_max + 1, 4);  // list + the zero slot
+  const int lmax = round_up(c.tl_max, 4);
   auto kern = k_cg_apply_tc<ND, NQ, BF16, HAS_K, X3, CURVED>;
   int dev = 0, smem_max = 0;
   TETMF_CK(cudaGetDevice(&dev));
@@ -759,7 +864,7 @@ int launch_g(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) 
   const void* img = X3 ? c.d_tc_tf32x3 : BF16 ? c.d_tc_bf16 : c.d_tc_tf32;
   kern<<<unsigned(grid), G * kT, sm, st>>>(c.d_tl_span, c.d_tl_list, c.d_tl_lidx, c.d_metric32,
                                            static_cast<const uint8_t*>(img), u, y, k, c.nc, c.ntiles, lmax, cols,
-                                           c.d_status, c.d_qmetric32);
+                                           c.d_status, c.d_qmetric32, c.ndofs, alignment_flags(u, y));
   TETMF_LAUNCH_CK();
   return FEM_OK;
 }
@@ -768,7 +873,7 @@ template <int ND, int NQ, bool BF16>
 int launch_ws(Ctx& c, const float* u, float* y, cudaStream_t st) {
   using S = TcShape<ND, NQ, BF16>;
   constexpr int G = ws_groups<ND, NQ, BF16>();
-  const int lmax = round_up(c.tl_max + 1, 4);
+  const int lmax = round_up(c.tl_max, 4);
   const size_t sm = size_t(S::B1_BYTES) + S::B2_BYTES + size_t(G) * S::A1_BYTES + 64 * G + 64 +
                     size_t(G) * 4 * stage_bytes<ND, NQ, false>(lmax);
   int dev = 0, smem_max = 0;
@@ -782,7 +887,8 @@ int launch_ws(Ctx& c, const float* u, float* y, cudaStream_t st) {
   if (grid > sm_count()) grid = sm_count();
   kern<<<unsigned(grid), (G + 1) * kT, sm, st>>>(c.d_tl_span, c.d_tl_list, c.d_tl_lidx, c.d_metric32,
                                                  static_cast<const uint8_t*>(BF16 ? c.d_tc_bf16 : c.d_tc_tf32), u, y,
-                                                 c.nc, c.ntiles, lmax, cols, c.d_status);
+                                                 c.nc, c.ntiles, lmax, cols, c.d_status, c.ndofs,
+                                                 alignment_flags(u, y));
   TETMF_LAUNCH_CK();
   return FEM_OK;
 }
@@ -791,7 +897,8 @@ template <int ND, int NQ, bool BF16, bool X3>
 int launch(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) {
   if (int e = init_rows<float>(y, u, c.d_mask, c.ndofs, 0.0f, st)) return e;
   if constexpr (!X3 && ws_groups<ND, NQ, BF16>() <= 3) {
-    // the warp-specialised kernel where TMEM leaves room for at most three tiles per SM
+    // where TMEM leaves room for at most three tiles per SM: compute warpgroups plus one warpgroup
+    // that moves the data
     if (!k) return launch_ws<ND, NQ, BF16>(c, u, y, st);
   }
   return k ? launch_g<ND, NQ, BF16, true, X3, false>(c, u, y, k, st)

@@ -79,34 +79,43 @@ int upload(Ctx& c) {
       }
     }
     if (int s = put(c, &c.d_idx, idx)) return s;
-    // tile-local lists: the tensor-core kernel gathers each distinct DoF of a
-    // tile once and pre-reduces the tile's contributions in shared memory
+    // tile-local lists: the tensor-core kernels move each tile's values in whole 16-byte groups
+    // of 4 consecutive DoFs (group g = DoFs 4g .. 4g+3).  Per tile: the sorted distinct groups that
+    // hold its unconstrained DoFs, and per (cell, local node) the node's position in the tile's
+    // staging, 4 x (the group's place in the list) + (DoF mod 4).  The DoF numbering (by the set of
+    // tiles sharing a DoF) makes these groups dense: about 4 of every 4.3 staged values are used.
     std::vector<int64_t> span(size_t(c.ntiles) * 2, 0);
     std::vector<int32_t> list;
     // node positions: per tile [ndp/2][128] pairs (node 2w in the low half, 2w+1 in the high half);
-    // constrained nodes, the padding node and the lanes past the last cell point at position L
-    // (one past the list), a slot the kernel keeps at zero on gather and never flushes
+    // constrained nodes, the padding node and the lanes past the last cell point at 4 L (L = groups
+    // in the list), a 4-value slot the kernel keeps at zero on gather and never flushes
     const int ndp = (c.nd + 1) / 2 * 2;
     std::vector<uint16_t> lidx(size_t(c.ntiles) * ndp * T, 0);
     std::vector<int32_t> buf;
-    list.reserve(size_t(c.nc) * 6);
+    list.reserve(size_t(c.nc) * 2);
     for (int64_t t = 0; t < c.ntiles; ++t) {
       buf.clear();
       const int64_t e1 = std::min<int64_t>(c.nc, (t + 1) * T);
       for (int64_t e = t * T; e < e1; ++e)
         for (int j = 0; j < c.nd; ++j) {
           const int32_t d = c.cell_dofs[size_t(e) * c.nd + j];
-          if (!c.mask[d]) buf.push_back(d);
+          if (!c.mask[d]) buf.push_back(d / 4);
         }
       std::sort(buf.begin(), buf.end());
       buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
-      std::fill(lidx.begin() + size_t(t) * ndp * T, lidx.begin() + size_t(t + 1) * ndp * T, uint16_t(buf.size()));
+      if (4 * buf.size() + 4 > 65535) {
+        set_error("a 128-cell batch touches %zu groups of DoFs (at most %d)", buf.size(), 65535 / 4 - 1);
+        return FEM_EUNSUPPORTED;
+      }
+      std::fill(lidx.begin() + size_t(t) * ndp * T, lidx.begin() + size_t(t + 1) * ndp * T,
+                uint16_t(4 * buf.size()));
       for (int64_t e = t * T; e < e1; ++e)
         for (int j = 0; j < c.nd; ++j) {
           const int32_t d = c.cell_dofs[size_t(e) * c.nd + j];
           if (c.mask[d]) continue;
-          const size_t pos = std::lower_bound(buf.begin(), buf.end(), d) - buf.begin();
-          lidx[size_t(t) * ndp * T + ((size_t(j) / 2) * T + (e - t * T)) * 2 + (j & 1)] = uint16_t(pos);
+          const size_t pos = std::lower_bound(buf.begin(), buf.end(), d / 4) - buf.begin();
+          lidx[size_t(t) * ndp * T + ((size_t(j) / 2) * T + (e - t * T)) * 2 + (j & 1)] =
+              uint16_t(4 * pos + (d & 3));
         }
       c.tl_max = std::max<int32_t>(c.tl_max, int32_t(buf.size()));
       span[2 * t] = int64_t(list.size());

@@ -80,12 +80,13 @@ struct Ctx {
   int32_t* d_fb_code = nullptr;
   double* d_fb_geo64 = nullptr;
   float* d_fb_geo32 = nullptr;
-  // tile-local DoF lists (CG): distinct unconstrained DoFs of each tile, and
-  // each (cell, local node) as an index into its tile's list (0xFFFF = constrained)
+  // tile-local group lists (CG): the distinct 16-byte groups (DoFs 4g .. 4g+3) holding each tile's
+  // unconstrained DoFs, and each (cell, local node) as its position in the tile's staging
+  // (4 x the group's place in the list + DoF mod 4; constrained nodes use the zero slot 4 L)
   int64_t* d_tl_span = nullptr;     // [ntiles][2]: offset (a multiple of 4) and length of the list
-  int32_t* d_tl_list = nullptr;     // lists, each padded to a multiple of 4 entries
-  uint16_t* d_tl_lidx = nullptr;    // [ntiles][nd][kTile]
-  int32_t tl_max = 0;               // longest list
+  int32_t* d_tl_list = nullptr;     // group indices, each tile's list padded to a multiple of 4 entries
+  uint16_t* d_tl_lidx = nullptr;    // [ntiles][ndp / 2][kTile] pairs of 16-bit positions
+  int32_t tl_max = 0;               // longest list (groups)
   // tensor-core operand images (shared-memory byte images of E^T and E)
   void* d_tc_tf32 = nullptr;
   void* d_tc_bf16 = nullptr;

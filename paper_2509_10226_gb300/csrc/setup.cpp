@@ -374,16 +374,57 @@ int build_plan(Ctx& c, const fem_mesh_desc* m) {
     c.cell_dofs.resize(size_t(nc) * nd);
     c.dof_canon.resize(N);
     c.dof_keys.resize(size_t(N) * c.p);
-    int32_t next = 0;
-    for (int64_t pos = 0; pos < nc * nd; ++pos) {
-      const int64_t g = group_of[pos];
-      if (lib_of_group[g] < 0) {
-        lib_of_group[g] = next;
-        c.dof_canon[next] = g;
-        for (int r = 0; r < c.p; ++r) c.dof_keys[size_t(next) * c.p + r] = group_key[g].v[r];
-        ++next;
+    // DoF numbering by sharing class: every DoF is tagged with the increasing list of 128-cell
+    // batches (tiles) whose cells touch it, and DoFs are numbered in lexicographic order of these
+    // lists (a list sorts after the longer lists it is a prefix of), ties in first-touch order.  The
+    // DoFs one tile touches then form a few contiguous runs (its own classes in one run, and one run
+    // per class it shares with an earlier tile), which the tensor-core kernel moves with bulk copies
+    // and bulk reductions instead of one access per DoF.
+    {
+      std::vector<int64_t> first(N, -1);
+      std::vector<int32_t> cnt(N, 0), last(N, -1);
+      for (int64_t pos = 0; pos < nc * nd; ++pos) {
+        const int64_t g = group_of[pos];
+        const int32_t t = int32_t(pos / nd / kTile);
+        if (first[g] < 0) first[g] = pos;
+        if (last[g] != t) {
+          last[g] = t;
+          ++cnt[g];
+        }
       }
-      c.cell_dofs[pos] = lib_of_group[g];
+      std::vector<int64_t> off(N + 1, 0);
+      for (int64_t g = 0; g < N; ++g) off[g + 1] = off[g] + cnt[g];
+      std::vector<int32_t> tiles(static_cast<size_t>(off[N]));
+      std::fill(last.begin(), last.end(), -1);
+      std::vector<int64_t> fill(off.begin(), off.end() - 1);
+      for (int64_t pos = 0; pos < nc * nd; ++pos) {
+        const int64_t g = group_of[pos];
+        const int32_t t = int32_t(pos / nd / kTile);
+        if (last[g] != t) {
+          last[g] = t;
+          tiles[size_t(fill[g]++)] = t;
+        }
+      }
+      std::vector<int64_t> order(N);
+      std::iota(order.begin(), order.end(), int64_t(0));
+      std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        const int64_t na = off[a + 1] - off[a], nb = off[b + 1] - off[b];
+        for (int64_t i = 0;; ++i) {
+          if (i == na || i == nb) {
+            if (na != nb) return na > nb;  // a prefix sorts after the longer list
+            return first[a] < first[b];
+          }
+          const int32_t ta = tiles[size_t(off[a] + i)], tb = tiles[size_t(off[b] + i)];
+          if (ta != tb) return ta < tb;
+        }
+      });
+      for (int64_t r = 0; r < N; ++r) {
+        const int64_t g = order[r];
+        lib_of_group[g] = int32_t(r);
+        c.dof_canon[r] = g;
+        for (int q = 0; q < c.p; ++q) c.dof_keys[size_t(r) * c.p + q] = group_key[g].v[q];
+      }
+      for (int64_t pos = 0; pos < nc * nd; ++pos) c.cell_dofs[pos] = lib_of_group[group_of[pos]];
     }
 
     c.mask.assign(N, 0);

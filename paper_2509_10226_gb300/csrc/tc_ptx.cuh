@@ -71,6 +71,31 @@ __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, vola
   }
   return true;
 }
+// a counter in shared memory that only grows, written with release and read with acquire semantics
+// (CTA scope): unlike an mbarrier's phase parity it cannot alias when the writer runs ahead
+__device__ __forceinline__ void st_release_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+// bounded wait until the counter reaches target (same limit and abort flag as mbar_wait_ab)
+__device__ __forceinline__ bool count_wait_ab(uint32_t addr, uint32_t target, volatile int* abort,
+                                              uint64_t limit_ns = kWaitLimitNs) {
+  if (ld_acquire_u32(addr) >= target) return true;
+  const uint64_t t0 = global_ns();
+  while (ld_acquire_u32(addr) < target) {
+    if (*abort) return false;
+    if (global_ns() - t0 > limit_ns) {
+      *abort = 1;
+      return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
