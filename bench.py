@@ -427,7 +427,7 @@ def measure_fma_peaks(torch, stream):
     sink = torch.zeros(1, dtype=torch.float64, device="cuda")
     out = {}
     for kind, iters in (("fp64", 25_000), ("fp32", 1_600_000), ("fp32x2", 800_000)):
-        fma_probe(kind, iters // 10, sink, stream)
+        fma_probe(kind, iters // 80 * 8, sink, stream)
         best = 0.0
         for _ in range(3):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -212,7 +212,7 @@ int fem_selftest_wait(fem_ctx* ctx, int64_t limit_ns, int64_t* waited_ns);
 /* Arithmetic-throughput probe (no counterpart in the paper; it measures the
  * denominators of the FP64 and FP32 rooflines the SIMT applies are reported
  * against).  Launches 4 x (SM count) blocks of 256 threads on the current
- * device, each thread running `iters` (1..2^30) iterations of eight
+ * device, each thread running `iters` (a multiple of 8 in 8..2^30) iterations of eight
  * independent FMA chains: kind 0 = FP64 fma, 1 = FP32 fma, 2 = packed FP32x2
  * fma.  *flops (host) receives the floating-point operations launched (an FMA
  * counts 2).  sink: device double[1], written only in a case that cannot occur

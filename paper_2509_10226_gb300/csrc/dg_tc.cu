@@ -26,6 +26,8 @@
 // DoF values and face data of the next tiles are copied ahead (cp.async).
 // Boundary faces (2 % of the faces at 48^3) keep the FP32 SIMT kernel.
 #include <algorithm>
+#include <array>
+#include <cmath>
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -47,7 +49,6 @@ struct FaceShape {
   static constexpr int KE = round_up(ND, KSTEP);        // evaluation GEMM K
   static constexpr int KI = round_up(4 * NQF, KSTEP);   // integration GEMM K
   static constexpr int NI = round_up(ND, 16);           // integration GEMM N
-  static constexpr int QW = BF16 ? NE / 2 : NE;         // TMEM columns of the coefficients of one side
   static constexpr int TCOLS = round_up(2 * NE + 2 * NI, 16);
   static constexpr int GMAX = 512 / TCOLS < 4 ? 512 / TCOLS : 4;
   static constexpr int LBO_E = (NE / 8) * 128;
@@ -61,38 +62,30 @@ struct FaceShape {
   static_assert(KI <= NE, "coefficients must fit in the evaluation columns");
 };
 
-// Operand images: 4 minus evaluation tables (local face f), 24 plus evaluation tables
-// (local face f, orientation o: id 4 + 6 f + o), then the same 28 integration tables.
-
+// Operand images of local face 0 of the reference cell (every face is seen as local face 0 of
+// both relabelled cells, points in the same order): the evaluation table, then the integration
+// table (quadrature weights folded in).
 template <int ND, int NQF, bool BF16>
 std::vector<uint8_t> face_images(const RefTables& t) {
   using S = FaceShape<ND, NQF, BF16>;
-  std::vector<uint8_t> img(size_t(28) * S::E_BYTES + size_t(28) * S::I_BYTES, 0);
+  std::vector<uint8_t> img(size_t(S::E_BYTES) + size_t(S::I_BYTES), 0);
   auto off = [](int r, int k, int lbo) {
     return size_t((k / S::KC) * lbo + (r / 8) * 128 + (r % 8) * 16 + (k % S::KC) * S::ES);
   };
-  // table entry: c = 0 value, c = 1..3 reference gradient, at point qq of local face f
-  auto entry = [&](int f, int qq, int c, int j) {
-    return c == 0 ? t.Vf[(size_t(f) * NQF + qq) * ND + j] : t.Ef[((size_t(f) * NQF + qq) * 3 + (c - 1)) * ND + j];
+  // table entry: c = 0 value, c = 1..3 reference gradient, at point q of local face 0
+  auto entry = [&](int q, int c, int j) {
+    return c == 0 ? t.Vf[size_t(q) * ND + j] : t.Ef[(size_t(q) * 3 + (c - 1)) * ND + j];
   };
-  for (int id = 0; id < 28; ++id) {
-    const int f = id < 4 ? id : (id - 4) / 6;
-    const int o = id < 4 ? -1 : (id - 4) % 6;
-    uint8_t* E = img.data() + size_t(id) * S::E_BYTES;
-    uint8_t* I = img.data() + size_t(28) * S::E_BYTES + size_t(id) * S::I_BYTES;
-    std::vector<uint8_t> e(S::E_BYTES, 0), in(S::I_BYTES, 0);
-    for (int q = 0; q < NQF; ++q) {
-      const int qq = o < 0 ? q : t.fperm[o * NQF + q];  // plus side in the minus side's point order
-      for (int c = 0; c < 4; ++c)
-        for (int j = 0; j < ND; ++j) {
-          const double v = entry(f, qq, c, j);
-          put_elem<BF16>(e, off(4 * q + c, j, S::LBO_E), v);
-          put_elem<BF16>(in, off(j, 4 * q + c, S::LBO_I), v * t.wqf[q]);
-        }
-    }
-    std::memcpy(E, e.data(), e.size());
-    std::memcpy(I, in.data(), in.size());
-  }
+  std::vector<uint8_t> e(S::E_BYTES, 0), in(S::I_BYTES, 0);
+  for (int q = 0; q < NQF; ++q)
+    for (int c = 0; c < 4; ++c)
+      for (int j = 0; j < ND; ++j) {
+        const double v = entry(q, c, j);
+        put_elem<BF16>(e, off(4 * q + c, j, S::LBO_E), v);
+        put_elem<BF16>(in, off(j, 4 * q + c, S::LBO_I), v * t.wqf[q]);
+      }
+  std::memcpy(img.data(), e.data(), e.size());
+  std::memcpy(img.data() + S::E_BYTES, in.data(), in.size());
   return img;
 }
 
@@ -278,44 +271,51 @@ __global__ void __launch_bounds__(kT * cell_gmax<ND, NQ, BF16>(), 1)
 // ---- interior faces ---------------------------------------------------------
 constexpr int kMetaWords = 11 * kTile;  // one slot of face data (see issue_face_meta)
 
+// per warpgroup: the DoF values of both sides (one slot), their results on the way back to y
+// (the rows in the cells' own DoF order) and the face data (two slots); per CTA: the two tables and
+// the DoF permutations of the 24 relabellings
 template <int ND, int NQF, bool BF16>
 constexpr size_t face_wg_bytes() {
+  return 2 * 2 * size_t(kT) * ND * 4 + 2 * size_t(kMetaWords) * 4;
+}
+template <int ND, int NQF, bool BF16>
+constexpr size_t face_cta_bytes() {
   using S = FaceShape<ND, NQF, BF16>;
-  // tables, DoF values of both sides (one slot), face data (two slots)
-  return 2 * size_t(S::E_BYTES) + 2 * size_t(S::I_BYTES) + 2 * size_t(kT) * ND * 4 + 2 * size_t(kMetaWords) * 4;
+  return 128 + size_t(S::E_BYTES) + size_t(S::I_BYTES) + size_t(24) * round_up(ND, 16);
 }
 
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
-// face data of tile t into a slot [11][128]: cells of both sides, a- a+ 2|F| tau (5 KB), and
-// the tile's code in word 10 * 128
-__device__ __forceinline__ void issue_face_meta(uint32_t* slot, const int32_t* __restrict__ tcode,
-                                                const int32_t* __restrict__ tcell, const float* __restrict__ tgeo,
+// face data of tile t into a slot [11][128]: cells of both sides, the relabelling word, then
+// a- a+ 2|F| tau
+__device__ __forceinline__ void issue_face_meta(uint32_t* slot, const int32_t* __restrict__ tcell,
+                                                const int32_t* __restrict__ tperm, const float* __restrict__ tgeo,
                                                 int64_t t, int m) {
   for (int i = m; i < 2 * kT / 4; i += kT) cp_async16(slot + 4 * i, tcell + t * 2 * kT + 4 * i);
-  for (int i = m; i < 8 * kT / 4; i += kT) cp_async16(slot + 2 * kT + 4 * i, tgeo + t * 8 * kT + 4 * i);
-  if (m == 0) cp_async4(slot + 10 * kT, tcode + t);
+  for (int i = m; i < kT / 4; i += kT) cp_async16(slot + 2 * kT + 4 * i, tperm + t * kT + 4 * i);
+  for (int i = m; i < 8 * kT / 4; i += kT) cp_async16(slot + 3 * kT + 4 * i, tgeo + t * 8 * kT + 4 * i);
 }
 
-// one staged row of ND values (64-bit shared loads for even ND: rows 40 bytes apart then fill
-// the two wavefronts of a warp's request without bank conflicts)
+// the DoF permutation of a relabelling: PROW bytes per row in shared memory (old local DoF of each
+// new local DoF), held as 32-bit words; perm_at(w, j) is the old DoF of new DoF j
 template <int ND>
-__device__ __forceinline__ void load_row(const float* r, float* v) {
-  if constexpr (ND % 2 == 0) {
+constexpr int perm_row_bytes() {
+  return round_up(ND, 16);
+}
+template <int ND>
+__device__ __forceinline__ void load_perm(const int8_t* sP, uint32_t id, uint32_t* w) {
+  const uint4* r = reinterpret_cast<const uint4*>(sP + id * perm_row_bytes<ND>());
 #pragma unroll
-    for (int j = 0; j < ND / 2; ++j) {
-      const float2 t = reinterpret_cast<const float2*>(r)[j];
-      v[2 * j] = t.x, v[2 * j + 1] = t.y;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < ND; ++j) v[j] = r[j];
+  for (int q = 0; q < perm_row_bytes<ND>() / 16; ++q) {
+    const uint4 v = r[q];
+    w[4 * q] = v.x, w[4 * q + 1] = v.y, w[4 * q + 2] = v.z, w[4 * q + 3] = v.w;
   }
 }
+__device__ __forceinline__ int perm_at(const uint32_t* w, int j) { return int((w[j >> 2] >> (8 * (j & 3))) & 0xFFu); }
 
-// this thread's rows of the tile: the DoF values of its face's two cells
+// this thread's rows of the tile: the DoF values of its face's two cells, in the cells' own order
 template <int ND>
 __device__ __forceinline__ void issue_face_u(float* su, const float* __restrict__ u, int64_t cm, int64_t cp, int m) {
   float* dm = su + m * ND;
@@ -331,6 +331,22 @@ __device__ __forceinline__ void issue_face_u(float* su, const float* __restrict_
   } else {
 #pragma unroll
     for (int j = 0; j < ND; ++j) cp_async4(dm + j, a + j), cp_async4(dp + j, b + j);
+  }
+}
+
+// one staged row of ND values (64-bit shared loads for even ND: rows 40 bytes apart then fill
+// the two wavefronts of a warp's request without bank conflicts)
+template <int ND>
+__device__ __forceinline__ void load_row(const float* r, float* v) {
+  if constexpr (ND % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < ND / 2; ++j) {
+      const float2 t = reinterpret_cast<const float2*>(r)[j];
+      v[2 * j] = t.x, v[2 * j + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < ND; ++j) v[j] = r[j];
   }
 }
 
@@ -388,19 +404,21 @@ __device__ __forceinline__ void tmem_st_row(uint32_t taddr, const uint32_t* w) {
   if constexpr (W % 16 == 8) tmem_st8(taddr + (W - 8), w + (W - 8));
 }
 
-// One CTA = G warpgroups; warpgroup w of the grid takes a contiguous run of tiles (tiles are
-// sorted by code, so a warpgroup reloads its tables only when the code changes).
+// One CTA = G warpgroups sharing the two face-0 tables; warpgroup w of the grid takes a contiguous
+// run of tiles (faces in the order of their minus cells, so a run covers a compact set of cells).
 // TMEM per warpgroup: D- [0, NE), D+ [NE, 2 NE) (coefficients overwrite them in place),
 // Y- [2 NE, 2 NE + NI), Y+ [2 NE + NI, 2 NE + 2 NI).  The rows U-, U+ (the A operands of the
 // evaluation GEMMs) are stored by each thread into its own lane of the Y columns, which the
 // integration GEMMs overwrite only after the evaluation GEMMs have completed.
-// The DoF values of tile t+1 and the face data of tile t+2 are copied (cp.async) while tile t
-// is computed.
+// Each side's values enter in the relabelled cell's DoF order (a permuted read of the staged row)
+// and its results leave in the cell's own order (a permuted write to a row of shared memory, then
+// vector reductions).  The DoF values of tile t+1 and the face data of tile t+2 are copied
+// (cp.async) while tile t is computed.
 template <int ND, int NQF, bool BF16>
 __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
-    k_dg_face_tc(const int32_t* __restrict__ tcode, const int32_t* __restrict__ tcell, const float* __restrict__ tgeo,
-                 const uint8_t* __restrict__ img, const float* __restrict__ u, float* __restrict__ y, int64_t ntiles,
-                 uint32_t tmem_cols, int32_t* __restrict__ status) {
+    k_dg_face_tc(const int32_t* __restrict__ tcell, const int32_t* __restrict__ tperm, const float* __restrict__ tgeo,
+                 const int8_t* __restrict__ dperm, const uint8_t* __restrict__ img, const float* __restrict__ u,
+                 float* __restrict__ y, int64_t ntiles, uint32_t tmem_cols, int32_t* __restrict__ status) {
   using S = FaceShape<ND, NQF, BF16>;
   constexpr int AW = BF16 ? S::KE / 2 : S::KE;  // TMEM columns of one row of U
   static_assert(AW <= S::NI && AW % 8 == 0, "rows of U must fit in the Y columns");
@@ -410,43 +428,50 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
   const int m = threadIdx.x % kT;
   const int warp = threadIdx.x >> 5;
   uint8_t* misc = smem;
-  uint8_t* sEm = smem + 128 + size_t(g) * face_wg_bytes<ND, NQF, BF16>();
-  uint8_t* sEp = sEm + S::E_BYTES;
-  uint8_t* sIm = sEp + S::E_BYTES;
-  uint8_t* sIp = sIm + S::I_BYTES;
-  float* sU = reinterpret_cast<float*>(sIp + S::I_BYTES);           // [2 sides][128][ND] (own rows)
-  uint32_t* sMeta = reinterpret_cast<uint32_t*>(sU + 2 * kT * ND);  // [2][kMetaWords]
+  uint8_t* sE = smem + 128;
+  uint8_t* sI = sE + S::E_BYTES;
+  int8_t* sP = reinterpret_cast<int8_t*>(sI + S::I_BYTES);  // [24][perm_row_bytes]
+  uint8_t* wg = smem + face_cta_bytes<ND, NQF, BF16>() + size_t(g) * face_wg_bytes<ND, NQF, BF16>();
+  float* sU = reinterpret_cast<float*>(wg);                         // [2 sides][128][ND] (own rows)
+  float* sR = sU + 2 * kT * ND;                                      // [2 sides][128][ND] results
+  uint32_t* sMeta = reinterpret_cast<uint32_t*>(sR + 2 * kT * ND);  // [2][kMetaWords]
   uint64_t* bar = reinterpret_cast<uint64_t*>(misc + 16 * g);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 64);
   const uint32_t bar_a = smem_u32(bar);
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(img);
+    uint4* dst = reinterpret_cast<uint4*>(sE);
+    for (int i = threadIdx.x; i < (S::E_BYTES + S::I_BYTES) / 16; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < 24 * perm_row_bytes<ND>(); i += blockDim.x) sP[i] = dperm[i];
+  }
   if (m == 0) mbar_init(bar_a);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  fence_proxy_async();  // the tables (generic writes) are read by the tensor cores
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot + uint32_t(g * S::TCOLS);
   const uint32_t lane_base = tmem + (uint32_t((warp & 3) * 32) << 16);
   constexpr uint32_t YM = 2 * S::NE, YP = 2 * S::NE + S::NI;  // Y- / U- and Y+ / U+ columns
-  const uint32_t aEm = smem_u32(sEm), aEp = smem_u32(sEp), aIm = smem_u32(sIm), aIp = smem_u32(sIp);
+  const uint32_t aE = smem_u32(sE), aI = smem_u32(sI);
   const int64_t nw = int64_t(gridDim.x) * G;
   const int64_t per = (ntiles + nw - 1) / nw;
   const int64_t t0 = (int64_t(blockIdx.x) * G + g) * per;
   const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
   uint32_t phase = 0;
   bool failed = false;
-  int code_loaded = -1;
   if (t0 < t1) {
     // prologue: face data of t0, then the values of t0 and the face data of t0+1
-    issue_face_meta(sMeta, tcode, tcell, tgeo, t0, m);
+    issue_face_meta(sMeta, tcell, tperm, tgeo, t0, m);
     cp_async_commit();
     cp_async_wait_group<0>();
     wg_sync(g);
     issue_face_u<ND>(sU, u, int64_t(int32_t(sMeta[m])), int64_t(int32_t(sMeta[kT + m])), m);
-    if (t0 + 1 < t1) issue_face_meta(sMeta + kMetaWords, tcode, tcell, tgeo, t0 + 1, m);
+    if (t0 + 1 < t1) issue_face_meta(sMeta + kMetaWords, tcell, tperm, tgeo, t0 + 1, m);
     cp_async_commit();
   }
   for (int64_t t = t0; t < t1; ++t) {
@@ -455,34 +480,23 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
     uint32_t* meta_next = sMeta + (sl ^ 1) * kMetaWords;
     cp_async_wait_group<0>();  // this tile's values (own rows) and the next tile's face data
     wg_sync(g);
-    // face data of the tile: cells of both sides, a- a+ 2|F| tau
+    // face data of the tile: cells of both sides, relabellings, a- a+ 2|F| tau
     const int64_t cm = int32_t(meta[m]), cp = int32_t(meta[kT + m]);
+    const uint32_t rl = meta[2 * kT + m];
     float geo[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) geo[r] = __uint_as_float(meta[(2 + r) * kT + m]);
-    const int code = int32_t(meta[10 * kT]);
-    if (code != code_loaded) {
-      // the four tables of this code (every MMA of the previous tile has completed)
-      const int fm = code / 24, fp = (code / 6) % 4, o = code % 6;
-      const uint4* ev = reinterpret_cast<const uint4*>(img);
-      const uint4* in = reinterpret_cast<const uint4*>(img + size_t(28) * S::E_BYTES);
-      constexpr int E16 = S::E_BYTES / 16, I16 = S::I_BYTES / 16;
-      for (int i = m; i < E16; i += kT) {
-        reinterpret_cast<uint4*>(sEm)[i] = __ldg(ev + size_t(fm) * E16 + i);
-        reinterpret_cast<uint4*>(sEp)[i] = __ldg(ev + size_t(4 + 6 * fp + o) * E16 + i);
-      }
-      for (int i = m; i < I16; i += kT) {
-        reinterpret_cast<uint4*>(sIm)[i] = __ldg(in + size_t(fm) * I16 + i);
-        reinterpret_cast<uint4*>(sIp)[i] = __ldg(in + size_t(4 + 6 * fp + o) * I16 + i);
-      }
-      fence_proxy_async();
-      code_loaded = code;
-    }
-    // 1. rows of U- and U+ (shifted by the minus side's first value) into this thread's TMEM lane
+    for (int r = 0; r < 8; ++r) geo[r] = __uint_as_float(meta[(3 + r) * kT + m]);
+    // 1. rows of U- and U+ in the relabelled DoF order (permuted reads of the staged rows, shifted
+    //    by the minus side's first value) into this thread's TMEM lane
+    uint32_t wm[perm_row_bytes<ND>() / 4], wp[perm_row_bytes<ND>() / 4];
+    load_perm<ND>(sP, rl & 0xFFu, wm);
+    load_perm<ND>(sP, (rl >> 8) & 0xFFu, wp);
     {
       float um[ND], up[ND];
-      load_row<ND>(sU + m * ND, um);
-      load_row<ND>(sU + (kT + m) * ND, up);
+      const float* rm = sU + m * ND;
+      const float* rp = sU + (kT + m) * ND;
+#pragma unroll
+      for (int j = 0; j < ND; ++j) um[j] = rm[perm_at(wm, j)], up[j] = rp[perm_at(wp, j)];
       const float sh = um[0];
       uint32_t w[AW];
       pack_row<ND, S::KE, BF16>(um, sh, w);
@@ -493,22 +507,21 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
     tmem_wait_st();
     tc_fence_before();
     wg_sync(g);
-    // 2. evaluation GEMMs: value and reference gradient of both sides at the minus side's points
+    // 2. evaluation GEMMs: value and reference gradient of both sides at the face's points
     if (m == 0) {
       tc_fence_after();
 #pragma unroll
-      for (int s = 0; s < S::KE / S::KSTEP; ++s) {
-        mma_ta<BF16>(tmem, tmem + YM + 8 * s, smem_desc(aEm + s * 2 * S::LBO_E, S::LBO_E, 128), S::idesc(S::NE),
-                     s > 0);
-        mma_ta<BF16>(tmem + S::NE, tmem + YP + 8 * s, smem_desc(aEp + s * 2 * S::LBO_E, S::LBO_E, 128),
-                     S::idesc(S::NE), s > 0);
+      for (int s2 = 0; s2 < S::KE / S::KSTEP; ++s2) {
+        const uint64_t be = smem_desc(aE + s2 * 2 * S::LBO_E, S::LBO_E, 128);
+        mma_ta<BF16>(tmem, tmem + YM + 8 * s2, be, S::idesc(S::NE), s2 > 0);
+        mma_ta<BF16>(tmem + S::NE, tmem + YP + 8 * s2, be, S::idesc(S::NE), s2 > 0);
       }
       mma_commit(bar_a);
     }
     // prefetch: values of tile t+1 (this thread's rows of tile t are consumed) and face data of
     // tile t+2 (into the slot read above, before the barrier)
     if (t + 1 < t1) issue_face_u<ND>(sU, u, int64_t(int32_t(meta_next[m])), int64_t(int32_t(meta_next[kT + m])), m);
-    if (t + 2 < t1) issue_face_meta(const_cast<uint32_t*>(meta), tcode, tcell, tgeo, t + 2, m);
+    if (t + 2 < t1) issue_face_meta(const_cast<uint32_t*>(meta), tcell, tperm, tgeo, t + 2, m);
     cp_async_commit();
     if (m == 0) failed |= !mbar_wait(bar_a, phase);
     phase ^= 1;
@@ -570,16 +583,15 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
     tmem_wait_st();
     tc_fence_before();
     wg_sync(g);
-    // 4. integration GEMMs (A = coefficients in TMEM, weights folded into the tables); they
+    // 4. integration GEMMs (A = coefficients in TMEM, weights folded into the table); they
     //    overwrite the rows of U, whose GEMMs have completed
     if (m == 0) {
       tc_fence_after();
 #pragma unroll
-      for (int s = 0; s < S::KI / S::KSTEP; ++s) {
-        mma_ta<BF16>(tmem + YM, tmem + 8 * s, smem_desc(aIm + s * 2 * S::LBO_I, S::LBO_I, 128), S::idesc(S::NI),
-                     s > 0);
-        mma_ta<BF16>(tmem + YP, tmem + S::NE + 8 * s, smem_desc(aIp + s * 2 * S::LBO_I, S::LBO_I, 128),
-                     S::idesc(S::NI), s > 0);
+      for (int s2 = 0; s2 < S::KI / S::KSTEP; ++s2) {
+        const uint64_t bi = smem_desc(aI + s2 * 2 * S::LBO_I, S::LBO_I, 128);
+        mma_ta<BF16>(tmem + YM, tmem + 8 * s2, bi, S::idesc(S::NI), s2 > 0);
+        mma_ta<BF16>(tmem + YP, tmem + S::NE + 8 * s2, bi, S::idesc(S::NI), s2 > 0);
       }
       mma_commit(bar_a);
       failed |= !mbar_wait(bar_a, phase);
@@ -588,7 +600,7 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
     failed = wg_any(g, failed);
     if (failed) break;
     tc_fence_after();
-    // 5. both rows added to y, one side at a time (padding faces have 2|F| = 0 and add nothing)
+    // 5. both rows back in the cells' own DoF order and added to y (padding faces have 2|F| = 0)
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
       uint32_t r[S::NI];
@@ -597,7 +609,16 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
       tmem_wait_ld();
 #pragma unroll
       for (int c = 0; c < S::NI / 16; ++c) reg_fence16(r + 16 * c);
-      if (geo[6] != 0.0f) red_cell<ND>(y + (side ? cp : cm) * ND, r);
+      const uint32_t* pw = side ? wp : wm;
+      float* row = sR + (side * kT + m) * ND;
+#pragma unroll
+      for (int j = 0; j < ND; ++j) row[perm_at(pw, j)] = __uint_as_float(r[j]);
+      float vf[ND];
+      load_row<ND>(row, vf);
+      uint32_t v[ND];
+#pragma unroll
+      for (int j = 0; j < ND; ++j) v[j] = __float_as_uint(vf[j]);
+      if (geo[6] != 0.0f) red_cell<ND>(y + (side ? cp : cm) * ND, v);
     }
     tc_fence_before();
   }
@@ -636,8 +657,8 @@ int launch_dg_tc(Ctx& c, const float* u, float* y, cudaStream_t st) {
   if (c.dg_ntiles > 0) {
     using S = FaceShape<ND, NQF, BF16>;
     int G = S::GMAX;
-    while (G > 1 && 128 + G * face_wg_bytes<ND, NQF, BF16>() > size_t(smem_max)) --G;
-    const size_t sm = 128 + G * face_wg_bytes<ND, NQF, BF16>();
+    while (G > 1 && face_cta_bytes<ND, NQF, BF16>() + G * face_wg_bytes<ND, NQF, BF16>() > size_t(smem_max)) --G;
+    const size_t sm = face_cta_bytes<ND, NQF, BF16>() + G * face_wg_bytes<ND, NQF, BF16>();
     if (sm > size_t(smem_max)) {
       set_error("DG tensor-core face kernel does not fit on an SM (%zu bytes of shared memory)", sm);
       return FEM_EUNSUPPORTED;
@@ -647,7 +668,7 @@ int launch_dg_tc(Ctx& c, const float* u, float* y, cudaStream_t st) {
     const uint32_t cols = uint32_t(pow2_cols(G * S::TCOLS));
     int64_t grid = (c.dg_ntiles + G - 1) / G;
     if (grid > sm_count()) grid = sm_count();
-    kern<<<unsigned(grid), G * kT, sm, st>>>(c.d_dgt_code, c.d_dgt_cell, c.d_dgt_geo,
+    kern<<<unsigned(grid), G * kT, sm, st>>>(c.d_dgt_cell, c.d_dgt_perm, c.d_dgt_geo, c.d_dg_dperm,
                                              static_cast<const uint8_t*>(BF16 ? c.d_dg_img_bf16 : c.d_dg_img_tf32),
                                              u, y, c.dg_ntiles, cols, c.d_status);
     TETMF_LAUNCH_CK();
@@ -658,31 +679,103 @@ int launch_dg_tc(Ctx& c, const float* u, float* y, cudaStream_t st) {
 }  // namespace
 
 int dg_tc_prepare(Ctx& c) {
-  // interior faces grouped by code, each group padded to whole tiles with zero-weight faces
-  std::vector<std::vector<int64_t>> groups(96);
-  for (int64_t i = 0; i < c.nfi; ++i) {
-    const int code = c.fi_code[i];
-    const int fm = code & 3, fp = (code >> 2) & 3, o = code >> 4;
-    groups[(fm * 4 + fp) * 6 + o].push_back(i);
+  // Every interior face is seen from both sides as local face 0 of a relabelled cell: new local
+  // vertex 0 is the one opposite the face, new vertices 1, 2, 3 are the face's vertices in
+  // increasing global order.  Both relabelled cells then place the face's quadrature points in the
+  // same order, one evaluation and one integration table serve every face, and tiles may hold any
+  // faces: they follow the minus cells' (Morton) order.  A relabelling is one of the 24
+  // permutations s of the four local vertices (new vertex i = old vertex s[i], lexicographic
+  // order of s); a new local DoF with multi-index b is the old one with multi-index b', b'[s[i]] = b[i].
+  static const int kFv[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  std::vector<std::array<int, 4>> perms;
+  {
+    std::array<int, 4> a = {0, 1, 2, 3};
+    do perms.push_back(a);
+    while (std::next_permutation(a.begin(), a.end()));
   }
-  int64_t nt = 0;
-  for (auto& g : groups) nt += (int64_t(g.size()) + kT - 1) / kT;
-  c.dg_ntiles = nt;
-  std::vector<int32_t> code(nt), cell(size_t(nt) * 2 * kT, 0);
-  std::vector<float> geo(size_t(nt) * 8 * kT, 0.0f);
-  int64_t t = 0;
-  for (int k = 0; k < 96; ++k) {
-    auto& g = groups[k];
-    std::sort(g.begin(), g.end(), [&](int64_t a, int64_t b) { return c.fi_cell[a] < c.fi_cell[b]; });
-    for (size_t s = 0; s < g.size(); s += kT, ++t) {
-      code[t] = k;
-      for (int m = 0; m < kT && s + m < g.size(); ++m) {
-        const int64_t i = g[s + m];
-        cell[(size_t(t) * 2 + 0) * kT + m] = c.fi_cell[i];
-        cell[(size_t(t) * 2 + 1) * kT + m] = c.fi_cell[c.nfi + i];
-        for (int r = 0; r < 8; ++r) geo[(size_t(t) * 8 + r) * kT + m] = float(c.fi_geo[size_t(r) * c.nfi + i]);
-      }
+  auto perm_id = [&](const std::array<int, 4>& s4) {
+    return int(std::lower_bound(perms.begin(), perms.end(), s4) - perms.begin());
+  };
+  std::vector<std::array<int, 4>> nodes;  // local DoF order: multi-indices, lexicographic
+  for (int b0 = 0; b0 <= c.p; ++b0)
+    for (int b1 = 0; b1 <= c.p - b0; ++b1)
+      for (int b2 = 0; b2 <= c.p - b0 - b1; ++b2) nodes.push_back({b0, b1, b2, c.p - b0 - b1 - b2});
+  const int nd = c.nd;
+  const int prow = (nd + 15) / 16 * 16;  // bytes per permutation row (16-byte aligned rows)
+  std::vector<int8_t> dperm(size_t(24) * prow, 0);
+  for (int id = 0; id < 24; ++id)
+    for (int j = 0; j < nd; ++j) {
+      std::array<int, 4> bo{};
+      for (int i = 0; i < 4; ++i) bo[perms[id][i]] = nodes[j][i];
+      dperm[size_t(id) * prow + j] = int8_t(std::find(nodes.begin(), nodes.end(), bo) - nodes.begin());
     }
+  auto lib_cell = [&](int64_t e) { return &c.ucells[size_t(4) * c.cell_perm[e]]; };
+  auto X = [&](int32_t v, int k) { return c.xyz[size_t(3) * v + k]; };
+  // J'^-1 n for the cell relabelled by s (J' = [x_s1 - x_s0 | x_s2 - x_s0 | x_s3 - x_s0])
+  auto jinv_n = [&](const int32_t* cv, const std::array<int, 4>& s4, const double n[3], double* a) {
+    double J[3][3];
+    for (int k = 0; k < 3; ++k)
+      for (int col = 0; col < 3; ++col) J[k][col] = X(cv[s4[col + 1]], k) - X(cv[s4[0]], k);
+    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    // a = J^-1 n by Cramer's rule
+    for (int col = 0; col < 3; ++col) {
+      double M[3][3];
+      for (int r = 0; r < 3; ++r)
+        for (int q = 0; q < 3; ++q) M[r][q] = q == col ? n[r] : J[r][q];
+      a[col] = (M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0])) /
+               det;
+    }
+  };
+  // interior faces in the order of their minus cell (then its local face)
+  std::vector<int64_t> order(c.nfi);
+  for (int64_t i = 0; i < c.nfi; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    const int32_t ca = c.fi_cell[a], cb = c.fi_cell[b];
+    return ca < cb || (ca == cb && (c.fi_code[a] & 3) < (c.fi_code[b] & 3));
+  });
+  const int64_t nt = (c.nfi + kT - 1) / kT;
+  c.dg_ntiles = nt;
+  std::vector<int32_t> cell(size_t(nt) * 2 * kT, 0), rl(size_t(nt) * kT, 0);
+  std::vector<float> geo(size_t(nt) * 8 * kT, 0.0f);
+  for (int64_t r = 0; r < c.nfi; ++r) {
+    const int64_t i = order[r], t = r / kT, m = r % kT;
+    const int32_t em = c.fi_cell[i], ep = c.fi_cell[c.nfi + i];
+    const int fm = c.fi_code[i] & 3, fp = (c.fi_code[i] >> 2) & 3;
+    const int32_t* vm = lib_cell(em);
+    const int32_t* vp = lib_cell(ep);
+    int32_t gv[3] = {vm[kFv[fm][0]], vm[kFv[fm][1]], vm[kFv[fm][2]]};
+    std::sort(gv, gv + 3);
+    std::array<int, 4> sm = {fm, 0, 0, 0}, sp = {fp, 0, 0, 0};
+    for (int q = 0; q < 3; ++q)
+      for (int a = 0; a < 4; ++a) {
+        if (vm[a] == gv[q]) sm[q + 1] = a;
+        if (vp[a] == gv[q]) sp[q + 1] = a;
+      }
+    // unit normal out of the minus cell
+    double e1[3], e2[3], n[3], o[3];
+    for (int k = 0; k < 3; ++k) {
+      e1[k] = X(gv[1], k) - X(gv[0], k);
+      e2[k] = X(gv[2], k) - X(gv[0], k);
+      o[k] = X(vm[fm], k) - X(gv[0], k);
+    }
+    n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    const double sgn = (n[0] * o[0] + n[1] * o[1] + n[2] * o[2]) > 0 ? -1.0 : 1.0;
+    for (int k = 0; k < 3; ++k) n[k] *= sgn / len;
+    double am[3], ap[3];
+    jinv_n(vm, sm, n, am);
+    jinv_n(vp, sp, n, ap);
+    cell[(size_t(t) * 2 + 0) * kT + m] = em;
+    cell[(size_t(t) * 2 + 1) * kT + m] = ep;
+    rl[size_t(t) * kT + m] = perm_id(sm) | (perm_id(sp) << 8);
+    const double g8[8] = {am[0], am[1], am[2], ap[0], ap[1], ap[2], c.fi_geo[size_t(6) * c.nfi + i],
+                          c.fi_geo[size_t(7) * c.nfi + i]};
+    for (int q = 0; q < 8; ++q) geo[(size_t(t) * 8 + q) * kT + m] = float(g8[q]);
   }
   auto up = [&](auto** dst, const auto& v) -> int {
     using T = typename std::remove_reference<decltype(v[0])>::type;
@@ -693,9 +786,10 @@ int dg_tc_prepare(Ctx& c) {
     *dst = static_cast<std::remove_const_t<T>*>(p);
     return FEM_OK;
   };
-  if (int s = up(&c.d_dgt_code, code)) return s;
   if (int s = up(&c.d_dgt_cell, cell)) return s;
+  if (int s = up(&c.d_dgt_perm, rl)) return s;
   if (int s = up(&c.d_dgt_geo, geo)) return s;
+  if (int s = up(&c.d_dg_dperm, dperm)) return s;
   switch (c.p) {
     case 1: return prepare_images<4, 4>(c);
     case 2: return prepare_images<10, 10>(c);

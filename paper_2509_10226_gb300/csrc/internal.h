@@ -92,11 +92,14 @@ struct Ctx {
   void* d_tc_bf16 = nullptr;
   void* d_tc_tf32x3 = nullptr;      // high then low TF32 parts (3xTF32)
   // DG tensor-core face loop: interior faces in tiles of 128 faces sharing (f-, f+, orientation)
+  // (faces in the order of their minus cells; each side's cell relabelled so that the face is its
+  // local face 0 with the face's vertices in increasing global order: one pair of tables for all)
   int64_t dg_ntiles = 0;
-  int32_t* d_dgt_code = nullptr;    // [dg_ntiles] (f- * 4 + f+) * 6 + o
   int32_t* d_dgt_cell = nullptr;    // [dg_ntiles][2][128] minus, plus (padding faces: 0, 0)
-  float* d_dgt_geo = nullptr;       // [dg_ntiles][8][128] a-(3) a+(3) 2|F| tau (padding: 0)
-  void* d_dg_img_tf32 = nullptr;    // face evaluation and integration tables (56 operand images)
+  int32_t* d_dgt_perm = nullptr;    // [dg_ntiles][128] relabelling of each side: minus | plus << 8
+  float* d_dgt_geo = nullptr;       // [dg_ntiles][8][128] a-(3) a+(3) 2|F| tau, relabelled frames (padding: 0)
+  int8_t* d_dg_dperm = nullptr;     // [24][nd rounded up to 16] old local DoF of each new local DoF, per relabelling
+  void* d_dg_img_tf32 = nullptr;    // face-0 evaluation and integration tables (2 operand images)
   void* d_dg_img_bf16 = nullptr;
   // CSR comparator
   int64_t csr_nnz = 0;

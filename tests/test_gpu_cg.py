@@ -132,22 +132,19 @@ def test_autograd_function():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16", "tf32x3"])
-def test_cg_p3_64cubed_full_size_sampled(prec):
+def test_cg_p3_64cubed_full_size(prec):
     """CG P3 on the 64^3 Kuhn cube (1,572,864 cells, 7,189,057 DoFs), Morton order, the launch the
-    benchmark times: 512 sampled rows against the oracle, plus A 1 = 0 and u^T A u = |a|^2."""
+    benchmark times: every entry of y against the oracle, plus A 1 = 0 and u^T A u = |a|^2."""
     from paper_2509_10226_gb300.fem import FemSpace
+    from tests import fullsize
 
     p = 3
-    xyz, cells = synth.kuhn_cube(64, jitter=0.2, seed=synth.SEEDS["jitter"])
+    xyz, cells, u_canon, y_canon = fullsize.cg_p3_64()
     sp = FemSpace(xyz, cells, degree=p, device=0)
     assert sp.n_dofs == 7189057
-    u = synth.uniform_vector(sp.n_dofs, synth.SEEDS["u"])  # drawn directly in library order
-    y = to_host(sp.apply(to_dev(u, prec), prec=prec))
-    rng = np.random.default_rng(11)
-    sample = rng.choice(sp.n_dofs, 512, replace=False)
-    y_ref = sampled_rows(sp, xyz, cells, p, u, sample)
-    # the sample's scale: rows of A u are O(h) sums with cancellation; compare against the sampled max
-    assert_close(y[sample], y_ref, prec, "CG P3 64^3 sampled")
+    perm = sp.dof_permutation()
+    y = to_host(sp.apply(to_dev(u_canon[perm], prec), prec=prec))
+    assert_close(y, y_canon[perm], prec, "CG P3 64^3")
     # properties that hold at any size
     ones = to_host(sp.apply(to_dev(np.ones(sp.n_dofs), prec), prec=prec))
     term = np.abs(y).max()
@@ -157,6 +154,7 @@ def test_cg_p3_64cubed_full_size_sampled(prec):
     lin = X @ a
     ylin = to_host(sp.apply(to_dev(lin, prec), prec=prec))
     assert abs(lin @ ylin - a @ a) <= 10 * TOL[prec] * (a @ a) + 1e-9
+    assert sp.device_status() == 0
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4])

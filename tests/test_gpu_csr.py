@@ -5,7 +5,7 @@ import pytest
 import synth
 from oracle import cg, topology
 from tests import brute
-from tests.gpu_util import assert_close, require_gpu, sampled_rows, to_dev, to_host
+from tests.gpu_util import assert_close, require_gpu, to_dev, to_host
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -44,17 +44,17 @@ def test_csr_matches_oracle(p, dirichlet):
 
 
 def test_csr_cg_p3_64cubed_full_size():
-    """P3 64^3 (314M stored entries): 512 sampled rows of the CSR SpMV against the oracle."""
+    """P3 64^3 (314M stored entries): every entry of the FP64 and FP32 CSR SpMV against the oracle's
+    matrix-free y = A u (the same operator)."""
     from paper_2509_10226_gb300.fem import FemSpace
+    from tests import fullsize
 
     p = 3
-    xyz, cells = synth.kuhn_cube(64, jitter=0.2, seed=synth.SEEDS["jitter"])
+    xyz, cells, u_canon, y_canon = fullsize.cg_p3_64()
     sp = FemSpace(xyz, cells, degree=p, device=0)
     nnz = sp.csr_build()
     assert 40 * sp.n_dofs < nnz < 50 * sp.n_dofs
-    u = synth.uniform_vector(sp.n_dofs, synth.SEEDS["u"])
-    sample = np.random.default_rng(13).choice(sp.n_dofs, 512, replace=False)
-    y_ref = sampled_rows(sp, xyz, cells, p, u, sample)
+    perm = sp.dof_permutation()
     for prec in ("fp64", "fp32"):
-        y = to_host(sp.csr_apply(to_dev(u, prec), prec=prec))
-        assert_close(y[sample], y_ref, prec, "csr CG P3 64^3 sampled")
+        y = to_host(sp.csr_apply(to_dev(u_canon[perm], prec), prec=prec))
+        assert_close(y, y_canon[perm], prec, "csr CG P3 64^3")
