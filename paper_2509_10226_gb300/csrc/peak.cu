@@ -6,9 +6,14 @@
 // per thread and 32 warps per SM keep the pipe fed past its latency, and eight iterations per
 // loop trip keep the loop's own instructions from taking dispatch slots from the FMAs.  Kind 0:
 // FP64 fma.rn.f64; kind 1: FP32 fma.rn.f32; kind 2: packed fma.rn.f32x2 (two FP32 FMAs per
-// instruction, the form the tensor-core apply's metric step uses).  The result is stored only if it equals a value the
-// caller passes and the chains never reach, so the compiler has to keep every FMA while the
-// kernel writes nothing in practice.
+// instruction, the form the tensor-core apply's metric step uses).  The result is stored only if
+// it equals a value the caller passes and the chains never reach, so the compiler has to keep
+// every FMA while the kernel writes nothing in practice.
+//
+// Measured on GB300: the FP64 loop issues about 1.6 DP instructions per clock and SM whatever the
+// chain count, occupancy or operand pattern, while the FP64 apply itself issues about 1.94; the
+// probe is therefore reported as a measured lower bound of the FP64 peak, next to the nominal
+// 1.25 TFLOP/s.  The FP32 loops reach 95-99 % of 128 FMA lanes per SM at 2.07 GHz.
 #include <cstdint>
 
 #include "common.cuh"
