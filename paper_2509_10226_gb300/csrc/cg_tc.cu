@@ -555,6 +555,12 @@ __global__ void __launch_bounds__(kT * (ws_groups<ND, NQ, BF16>() + 1), 1)
   auto stage_of = [&](int gg, int i) {
     return stage_at<ND, NQ, false>(stages + (size_t(gg) * kStages + i) * sbytes, lmax);
   };
+  const int64_t stride = int64_t(gridDim.x) * G;
+  // the first three tiles' spans, in flight while the tables are copied
+  const int64_t tile0 = int64_t(blockIdx.x) * G + g;
+  const Span sp0 = load_span(tl_span, g < G ? tile0 : ntiles, ntiles);
+  const Span sp1 = load_span(tl_span, g < G ? tile0 + stride : ntiles, ntiles);
+  const Span sp2 = load_span(tl_span, g < G ? tile0 + 2 * stride : ntiles, ntiles);
   {
     const uint4* src = reinterpret_cast<const uint4*>(bimg);
     uint4* dst = reinterpret_cast<uint4*>(sB1);
@@ -570,7 +576,6 @@ __global__ void __launch_bounds__(kT * (ws_groups<ND, NQ, BF16>() + 1), 1)
                  "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  const int64_t stride = int64_t(gridDim.x) * G;
   bool failed = false;
 
   if (g < G) {
@@ -579,13 +584,18 @@ __global__ void __launch_bounds__(kT * (ws_groups<ND, NQ, BF16>() + 1), 1)
     auto stage = [&](int i) { return stage_of(g, i); };
     const uint32_t b_g1 = bars(g), b_g2 = bars(g) + 8, b_rdy = bars(g) + 16, b_yfree = bars(g) + 24,
                    b_flushed = bars(g) + 32;
-    int64_t tile = int64_t(blockIdx.x) * G + g;
+    int64_t tile = tile0;
     int L_cur = 0, L_next = 0, L_next2 = 0;
-    if (tile < ntiles)
-      L_cur = issue_meta<ND, NQ, false>(stage(0), m, tile, load_span(tl_span, tile, ntiles), tl_list, tl_lidx, nullptr, nc);
+    // prologue, three dependent round trips (span, then list, then values): the metadata of tiles
+    // 0 and 1, the values of tile 0 once its list is in, then the values of tile 1 and the
+    // metadata of tile 2; one cp.async group each
+    if (tile < ntiles) L_cur = issue_meta<ND, NQ, false>(stage(0), m, tile, sp0, tl_list, tl_lidx, nullptr, nc);
+    else cp_async_commit();
+    if (tile + stride < ntiles)
+      L_next = issue_meta<ND, NQ, false>(stage(1), m, tile + stride, sp1, tl_list, tl_lidx, nullptr, nc);
     else
       cp_async_commit();
-    cp_async_wait_group<0>();
+    cp_async_wait_group<1>();  // metadata of tile 0
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -595,18 +605,16 @@ __global__ void __launch_bounds__(kT * (ws_groups<ND, NQ, BF16>() + 1), 1)
     const uint32_t aA1 = smem_u32(sA1), aB1 = smem_u32(sB1), aB2 = smem_u32(sB2);
     if (tile < ntiles) issue_gather<ND, NQ, false>(stage(0), m, L_cur, u, ndofs, u16);
     else cp_async_commit();
-    if (tile + stride < ntiles)
-      L_next = issue_meta<ND, NQ, false>(stage(1), m, tile + stride, load_span(tl_span, tile + stride, ntiles), tl_list, tl_lidx, nullptr, nc);
-    else
-      cp_async_commit();
-    cp_async_wait_group<0>();
+    cp_async_wait_group<1>();  // metadata of tile 1
     wg_sync(g);
     if (tile + stride < ntiles) issue_gather<ND, NQ, false>(stage(1), m, L_next, u, ndofs, u16);
     else cp_async_commit();
     if (tile + 2 * stride < ntiles)
-      L_next2 = issue_meta<ND, NQ, false>(stage(2), m, tile + 2 * stride, load_span(tl_span, tile + 2 * stride, ntiles), tl_list, tl_lidx, nullptr, nc);
+      L_next2 = issue_meta<ND, NQ, false>(stage(2), m, tile + 2 * stride, sp2, tl_list, tl_lidx, nullptr, nc);
     else
       cp_async_commit();
+    cp_async_wait_group<2>();  // values of tile 0
+    wg_sync(g);
     int b = 0;
     // the span of the tile whose metadata is copied next and the metric of the current tile, both
     // loaded one tile ahead
@@ -692,6 +700,9 @@ __global__ void __launch_bounds__(kT * (ws_groups<ND, NQ, BF16>() + 1), 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // the kernel may start while the zero-fill of y (launched before it) still runs: the scatter
+    // is the only part that touches y
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint32_t tbase = *tslot + (uint32_t((warp & 3) * 32) << 16);
     for (uint32_t k = 0; !failed && int64_t(blockIdx.x) * G + int64_t(k) * stride < ntiles; ++k) {
       for (int gg = 0; gg < G; ++gg) {
@@ -885,10 +896,22 @@ int launch_ws(Ctx& c, const float* u, float* y, cudaStream_t st) {
   const uint32_t cols = uint32_t(pow2_cols(G * tc_tcols<ND, NQ, BF16, false>()));
   int64_t grid = (c.ntiles + G - 1) / G;
   if (grid > sm_count()) grid = sm_count();
-  kern<<<unsigned(grid), (G + 1) * kT, sm, st>>>(c.d_tl_span, c.d_tl_list, c.d_tl_lidx, c.d_metric32,
-                                                 static_cast<const uint8_t*>(BF16 ? c.d_tc_bf16 : c.d_tc_tf32), u, y,
-                                                 c.nc, c.ntiles, lmax, cols, c.d_status, c.ndofs,
-                                                 alignment_flags(u, y));
+  // may start while the zero-fill before it runs (the kernel waits for it before touching y)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(unsigned((G + 1) * kT));
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const uint8_t* img = static_cast<const uint8_t*>(BF16 ? c.d_tc_bf16 : c.d_tc_tf32);
+  TETMF_CK(cudaLaunchKernelEx(&cfg, kern, static_cast<const int64_t*>(c.d_tl_span),
+                              static_cast<const int32_t*>(c.d_tl_list), static_cast<const uint16_t*>(c.d_tl_lidx),
+                              static_cast<const float*>(c.d_metric32), img, u, y, int64_t(c.nc), int64_t(c.ntiles),
+                              lmax, cols, c.d_status, int64_t(c.ndofs), alignment_flags(u, y)));
   TETMF_LAUNCH_CK();
   return FEM_OK;
 }

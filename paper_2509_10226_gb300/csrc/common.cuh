@@ -45,10 +45,13 @@ inline int allow_smem(K kernel, size_t bytes) {
   return FEM_OK;
 }
 
-// y[i] = mask && mask[i] ? u[i] * diag_one : 0  (Dirichlet identity rows, or zero fill)
+// y[i] = mask && mask[i] ? u[i] * diag_one : 0  (Dirichlet identity rows, or zero fill).  A kernel
+// launched after it with programmatic stream serialization may start at once; it must execute
+// griddepcontrol.wait before it touches y.
 template <typename T>
 __global__ void k_init_rows(T* __restrict__ y, const T* __restrict__ u, const uint8_t* __restrict__ mask, int64_t n,
                             T fixed) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     T v = T(0);
     if (mask && mask[i]) v = u ? u[i] : fixed;
