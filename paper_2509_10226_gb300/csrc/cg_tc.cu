@@ -310,7 +310,12 @@ __global__ void __launch_bounds__(kT * tc_max_groups<ND, NQ, BF16, X3, CURVED>()
   // receives at most 128 contributions (one per cell), so no sum overflows, and the quantum
   // 2^(E - 24) is below 1.2e-7 of the largest contribution.  Tiles with a non-finite contribution
   // fall back to float atomics.
+  bool fill_done = false;  // the zero-fill of y launched before this kernel (the first scatter waits)
   auto scatter = [&](const St& st, int Ls, const uint32_t* lwp) {
+    if (!fill_done) {
+      asm volatile("griddepcontrol.wait;" ::: "memory");
+      fill_done = true;
+    }
     uint32_t r[S::N2];
 #pragma unroll
     for (int c = 0; c < S::N2 / 16; ++c) tmem_ld16(lane_base + S::D2_COL + 16 * c, r + 16 * c);
@@ -873,9 +878,10 @@ int launch_g(Ctx& c, const float* u, float* y, const float* k, cudaStream_t st) 
   int64_t grid = (c.ntiles + G - 1) / G;
   if (grid > sm_count()) grid = sm_count();
   const void* img = X3 ? c.d_tc_tf32x3 : BF16 ? c.d_tc_bf16 : c.d_tc_tf32;
-  kern<<<unsigned(grid), G * kT, sm, st>>>(c.d_tl_span, c.d_tl_list, c.d_tl_lidx, c.d_metric32,
-                                           static_cast<const uint8_t*>(img), u, y, k, c.nc, c.ntiles, lmax, cols,
-                                           c.d_status, c.d_qmetric32, c.ndofs, alignment_flags(u, y));
+  // may start while the zero-fill before it runs (the first scatter waits for it)
+  TETMF_CK(launch_early(kern, dim3(unsigned(grid)), dim3(unsigned(G * kT)), sm, st, c.d_tl_span, c.d_tl_list,
+                        c.d_tl_lidx, c.d_metric32, static_cast<const uint8_t*>(img), u, y, k, c.nc, c.ntiles, lmax, cols,
+                        c.d_status, c.d_qmetric32, c.ndofs, alignment_flags(u, y)));
   TETMF_LAUNCH_CK();
   return FEM_OK;
 }
@@ -897,21 +903,9 @@ int launch_ws(Ctx& c, const float* u, float* y, cudaStream_t st) {
   int64_t grid = (c.ntiles + G - 1) / G;
   if (grid > sm_count()) grid = sm_count();
   // may start while the zero-fill before it runs (the kernel waits for it before touching y)
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(grid));
-  cfg.blockDim = dim3(unsigned((G + 1) * kT));
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  const uint8_t* img = static_cast<const uint8_t*>(BF16 ? c.d_tc_bf16 : c.d_tc_tf32);
-  TETMF_CK(cudaLaunchKernelEx(&cfg, kern, static_cast<const int64_t*>(c.d_tl_span),
-                              static_cast<const int32_t*>(c.d_tl_list), static_cast<const uint16_t*>(c.d_tl_lidx),
-                              static_cast<const float*>(c.d_metric32), img, u, y, int64_t(c.nc), int64_t(c.ntiles),
-                              lmax, cols, c.d_status, int64_t(c.ndofs), alignment_flags(u, y)));
+  TETMF_CK(launch_early(kern, dim3(unsigned(grid)), dim3(unsigned((G + 1) * kT)), sm, st, c.d_tl_span, c.d_tl_list,
+                        c.d_tl_lidx, c.d_metric32, static_cast<const uint8_t*>(BF16 ? c.d_tc_bf16 : c.d_tc_tf32), u, y,
+                        c.nc, c.ntiles, lmax, cols, c.d_status, c.ndofs, alignment_flags(u, y)));
   TETMF_LAUNCH_CK();
   return FEM_OK;
 }

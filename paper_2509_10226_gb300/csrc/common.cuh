@@ -32,6 +32,24 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // Number of SMs of the current device (cached per process for device 0..15).
 int sm_count();
 
+// Launch a kernel that may start while the kernel before it in the stream still runs (programmatic
+// dependent launch, once that kernel has executed griddepcontrol.launch_dependents or exited): the
+// launched kernel must execute griddepcontrol.wait before it touches anything its predecessor writes.
+template <typename... P, typename... A>
+inline cudaError_t launch_early(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<P>(args)...);
+}
+
 // Opt a kernel into more than 48 KB of dynamic shared memory (once per call site).
 template <typename K>
 inline int allow_smem(K kernel, size_t bytes) {

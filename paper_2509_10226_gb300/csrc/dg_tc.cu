@@ -136,6 +136,9 @@ __global__ void __launch_bounds__(kT * cell_gmax<ND, NQ, BF16>(), 1)
   using S = TcShape<ND, NQ, BF16>;
   constexpr int TCOLS = cell_tcols<ND, NQ, BF16>();
   extern __shared__ __align__(1024) uint8_t smem[];
+  // the face kernel launched after this one may start now; it waits for this kernel before it adds
+  // to y
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int G = blockDim.x / kT;
   const int g = threadIdx.x / kT;
   const int m = threadIdx.x % kT;
@@ -464,6 +467,7 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
   const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
   uint32_t phase = 0;
   bool failed = false;
+  bool cells_done = false;
   if (t0 < t1) {
     // prologue: face data of t0, then the values of t0 and the face data of t0+1
     issue_face_meta(sMeta, tcell, tperm, tgeo, t0, m);
@@ -600,7 +604,12 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
     failed = wg_any(g, failed);
     if (failed) break;
     tc_fence_after();
-    // 5. both rows back in the cells' own DoF order and added to y (padding faces have 2|F| = 0)
+    // 5. both rows back in the cells' own DoF order and added to y (padding faces have 2|F| = 0),
+    //    once the cell kernel before this one has written y
+    if (!cells_done) {
+      asm volatile("griddepcontrol.wait;" ::: "memory");
+      cells_done = true;
+    }
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
       uint32_t r[S::NI];
@@ -668,9 +677,11 @@ int launch_dg_tc(Ctx& c, const float* u, float* y, cudaStream_t st) {
     const uint32_t cols = uint32_t(pow2_cols(G * S::TCOLS));
     int64_t grid = (c.dg_ntiles + G - 1) / G;
     if (grid > sm_count()) grid = sm_count();
-    kern<<<unsigned(grid), G * kT, sm, st>>>(c.d_dgt_cell, c.d_dgt_perm, c.d_dgt_geo, c.d_dg_dperm,
-                                             static_cast<const uint8_t*>(BF16 ? c.d_dg_img_bf16 : c.d_dg_img_tf32),
-                                             u, y, c.dg_ntiles, cols, c.d_status);
+    // may start while the cell kernel runs (it waits for it before adding to y)
+    TETMF_CK(launch_early(kern, dim3(unsigned(grid)), dim3(unsigned(G * kT)), sm, st, c.d_dgt_cell, c.d_dgt_perm,
+                          c.d_dgt_geo, c.d_dg_dperm,
+                          static_cast<const uint8_t*>(BF16 ? c.d_dg_img_bf16 : c.d_dg_img_tf32), u, y, c.dg_ntiles,
+                          cols, c.d_status));
     TETMF_LAUNCH_CK();
   }
   return dg_boundary_fp32(c, u, y, st);
