@@ -425,6 +425,8 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
   using S = FaceShape<ND, NQF, BF16>;
   constexpr int AW = BF16 ? S::KE / 2 : S::KE;  // TMEM columns of one row of U
   static_assert(AW <= S::NI && AW % 8 == 0, "rows of U must fit in the Y columns");
+  // the boundary-face kernel launched after this one may start now; it waits for this kernel
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   extern __shared__ __align__(1024) uint8_t smem[];
   const int G = blockDim.x / kT;
   const int g = threadIdx.x / kT;
