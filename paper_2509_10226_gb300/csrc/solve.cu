@@ -49,6 +49,48 @@ struct Work {
   double* host_scal;     // pinned host mirror
 };
 
+// A block of kCheck PCG iterations (apply, dot, update, direction each) captured once per solve
+// into a CUDA graph and replayed with one launch per block: the host then enqueues one graph per
+// residual check instead of about 6 kCheck kernels and their attribute queries, which is what the
+// iterations cost at the smaller sizes.  kCheck is even, so the two alternating scalar slots of
+// the recurrence line up from one block to the next.  A capture or instantiation that fails leaves
+// the plain loop in charge.
+struct PcgGraph {
+  bool enabled = false;  // fem_solve: yes; fem_solve_noalloc: no (instantiating a graph may allocate)
+  bool failed = false;
+  cudaGraphExec_t exec = nullptr;
+  ~PcgGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+static_assert(kCheck % 2 == 0, "graph blocks must keep the scalar slots' parity");
+
+// record what body(stream) enqueues into g.exec, on a private stream; on any failure g.failed
+template <typename Body>
+void capture_block(PcgGraph& g, Body body) {
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    g.failed = true;
+    return;
+  }
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    const int body_status = body(cs);
+    ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && body_status == FEM_OK && graph != nullptr;
+  }
+  if (ok) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (!ok) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.failed = true;
+    cudaGetLastError();  // a failed capture leaves no error behind for later calls
+  }
+}
+
 
 
 
@@ -139,28 +181,52 @@ int read_scalar(const double* dev, double* host, double& out, cudaStream_t st) {
   return FEM_OK;
 }
 
-// Jacobi-PCG on vectors of type T with the operator `apply` (y = A x);
-// solves A x = r starting from x = 0 (r is overwritten by the residual).
+// Jacobi-PCG on vectors of type T with the operator `apply` (y = A x, apply(x, y, stream));
+// solves A x = r starting from x = 0 (r is overwritten by the residual).  With g.enabled, whole
+// blocks of kCheck iterations run as one graph launch.
 template <typename T, typename Apply>
 int pcg(const char* who, Ctx& c, Work& w, Apply apply, T* x, T* r, T* z, T* p, T* q, const T* diag,
-        double rtol_abs2, int max_it, int& iters, cudaStream_t st) {
+        double rtol_abs2, int max_it, int& iters, cudaStream_t st, PcgGraph& g) {
   const int64_t N = c.ndofs;
   const int rg = red_grid(N), eg = ew_grid(N);
   k_pcg_start<T><<<rg, kBlock, 0, st>>>(r, diag, z, p, N, w.partials, w.ticket, w.scal + S_RZ0, w.scal + S_RR);
   TETMF_LAUNCH_CK();
+  // iteration `it` of the recurrence on stream s
+  auto iteration = [&](int it, cudaStream_t s) -> int {
+    const int cur = S_RZ0 + (it & 1), nxt = S_RZ0 + ((it + 1) & 1);
+    if (int e = apply(p, q, s)) return e;
+    k_dot<T><<<rg, kBlock, 0, s>>>(p, q, N, w.partials, w.ticket, w.scal + S_PQ);
+    TETMF_LAUNCH_CK();
+    k_pcg_update<T><<<rg, kBlock, 0, s>>>(x, r, z, p, q, diag, N, w.scal + cur, w.scal + S_PQ, w.partials, w.ticket,
+                                          w.scal + nxt, w.scal + S_RR);
+    TETMF_LAUNCH_CK();
+    k_pcg_direction<T><<<eg, kBlock, 0, s>>>(p, z, N, w.scal + nxt, w.scal + cur);
+    TETMF_LAUNCH_CK();
+    return FEM_OK;
+  };
   double rr = 0.0;
   if (int e = read_scalar(w.scal + S_RR, w.host_scal, rr, st)) return e;
   iters = 0;
   while (rr > rtol_abs2 && iters < max_it) {
-    const int cur = S_RZ0 + (iters & 1), nxt = S_RZ0 + ((iters + 1) & 1);
-    if (int e = apply(p, q)) return e;
-    k_dot<T><<<rg, kBlock, 0, st>>>(p, q, N, w.partials, w.ticket, w.scal + S_PQ);
-    TETMF_LAUNCH_CK();
-    k_pcg_update<T><<<rg, kBlock, 0, st>>>(x, r, z, p, q, diag, N, w.scal + cur, w.scal + S_PQ, w.partials, w.ticket,
-                                           w.scal + nxt, w.scal + S_RR);
-    TETMF_LAUNCH_CK();
-    k_pcg_direction<T><<<eg, kBlock, 0, st>>>(p, z, N, w.scal + nxt, w.scal + cur);
-    TETMF_LAUNCH_CK();
+    if (g.enabled && !g.failed && iters % kCheck == 0 && iters + kCheck <= max_it) {
+      if (!g.exec)
+        capture_block(g, [&](cudaStream_t cs) -> int {
+          for (int k = 0; k < kCheck; ++k)
+            if (int e = iteration(k, cs)) return e;
+          return FEM_OK;
+        });
+      if (g.exec) {
+        TETMF_CK(cudaGraphLaunch(g.exec, st));
+        iters += kCheck;
+        if (int e = read_scalar(w.scal + S_RR, w.host_scal, rr, st)) return e;
+        if (!std::isfinite(rr)) {
+          set_error("%s: residual is not finite after %d iterations", who, iters);
+          return FEM_ENOTCONV;
+        }
+        continue;
+      }
+    }
+    if (int e = iteration(iters, st)) return e;
     ++iters;
     // the host reads the residual every kCheck iterations only (one synchronisation); the
     // iterations run past convergence keep reducing it (a zero denominator yields a zero step)
@@ -178,8 +244,9 @@ int pcg(const char* who, Ctx& c, Work& w, Apply apply, T* x, T* r, T* z, T* p, T
 
 // the solver proper, on work arrays laid out by carve()
 // who: the entry point's name, for the error messages
+// graphs: replay blocks of inner iterations as CUDA graphs (fem_solve; fem_solve_noalloc does not)
 static int solve_with(const char* who, Ctx& c, Work& w, const fem_solve_opts* o, const double* b, double* x,
-                      fem_solve_stats* stats, void* stream) {
+                      fem_solve_stats* stats, void* stream, bool graphs) {
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = as_stream(stream);
   const int64_t N = c.ndofs;
@@ -219,9 +286,11 @@ static int solve_with(const char* who, Ctx& c, Work& w, const fem_solve_opts* o,
   double rel = 0.0;
   if (o->mode == FEM_SOLVE_FP64_PCG) {
     if (int e = residual(rel)) return e;
-    auto apply64 = [&](double* in, double* out) {
-      return cg_apply_simt(c, FEM_FP64, in, out, nullptr, false, stream);
+    auto apply64 = [&](double* in, double* out, cudaStream_t s) {
+      return cg_apply_simt(c, FEM_FP64, in, out, nullptr, false, s);
     };
+    PcgGraph g;
+    g.enabled = graphs;
     // PCG stops on its recurrence residual; the true residual b - A x is then recomputed, and where
     // rounding has left it above the tolerance PCG restarts from x with it (at most 8 restarts,
     // within the same iteration cap)
@@ -229,7 +298,7 @@ static int solve_with(const char* who, Ctx& c, Work& w, const fem_solve_opts* o,
     for (int pass = 0;; ++pass) {
       int it = 0;
       const int e = pcg<double>(who, c, w, apply64, x, w.r64, w.z64, w.p64, w.t64, w.diag64, o->rtol * o->rtol * bb,
-                                o->max_inner - total, it, st);
+                                o->max_inner - total, it, st, g);
       total += it;
       stats->inner_iterations = total;
       stats->outer_iterations = pass + 1;
@@ -249,10 +318,12 @@ static int solve_with(const char* who, Ctx& c, Work& w, const fem_solve_opts* o,
   float* q32 = static_cast<float*>(w.q);
   float* d32 = static_cast<float*>(w.d);
   const int ip = o->inner_prec;
-  auto apply32 = [&](float* in, float* out) {
-    return ip == FEM_FP32 ? cg_apply_simt(c, FEM_FP32, in, out, nullptr, false, stream)
-                          : cg_apply_tc(c, ip, in, out, nullptr, stream);
+  auto apply32 = [&](float* in, float* out, cudaStream_t s) {
+    return ip == FEM_FP32 ? cg_apply_simt(c, FEM_FP32, in, out, nullptr, false, s)
+                          : cg_apply_tc(c, ip, in, out, nullptr, s);
   };
+  PcgGraph g;
+  g.enabled = graphs;
   const double inner = o->inner_rtol > 0 ? o->inner_rtol : 1e-3;
   const bool pmg = o->mode == FEM_SOLVE_IR_PMG;
   if (pmg)
@@ -267,7 +338,7 @@ static int solve_with(const char* who, Ctx& c, Work& w, const fem_solve_opts* o,
     int it = 0;
     const int e = pmg ? pmg_inner_solve(c, w.diag32, r32, d32, p32, q32, inner, o->max_inner, it, stream)
                       : pcg<float>(who, c, w, apply32, d32, r32, z32, p32, q32, w.diag32, inner * inner, o->max_inner, it,
-                                   st);
+                                   st, g);
     stats->inner_iterations += it;
     stats->outer_iterations += 1;
     if (e && e != FEM_ENOTCONV) return e;
@@ -279,7 +350,7 @@ static int solve_with(const char* who, Ctx& c, Work& w, const fem_solve_opts* o,
 int solve(Ctx& c, const fem_solve_opts* o, const double* b, double* x, fem_solve_stats* stats, void* stream) {
   Work w;
   if (int e = ensure_work(c, w)) return e;
-  return solve_with("fem_solve", c, w, o, b, x, stats, stream);
+  return solve_with("fem_solve", c, w, o, b, x, stats, stream, true);
 }
 
 }  // namespace tetmf
@@ -375,5 +446,5 @@ extern "C" int fem_solve_noalloc(fem_ctx* ctx, const fem_solve_opts* opts, const
   TETMF_CK(cudaMemsetAsync(w.ticket, 0, 64, as_stream(stream)));
   static thread_local double host_scal[S_COUNT];
   w.host_scal = host_scal;
-  return solve_with("fem_solve_noalloc", c, w, opts, b, x, stats, stream);
+  return solve_with("fem_solve_noalloc", c, w, opts, b, x, stats, stream, false);
 }
