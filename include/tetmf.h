@@ -356,7 +356,10 @@ typedef struct {
  * double[N]; x holds the initial guess on entry and the last iterate on
  * return.  Work vectors are allocated by the context on the first call and
  * kept.  Runs on `stream` and synchronises it.  Returns FEM_ENOTCONV (x still
- * valid, stats filled) if a cap is hit. */
+ * valid, stats filled) if a cap is hit.  The Jacobi-PCG iterations run in
+ * blocks of eight recorded once per call into a CUDA graph (captured on a
+ * private stream of the library, replayed on `stream`); where the capture
+ * fails, the same iterations run as plain launches. */
 int fem_solve(fem_ctx* ctx, const fem_solve_opts* opts, const double* b, double* x,
               fem_solve_stats* stats, void* stream);
 
