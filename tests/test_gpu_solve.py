@@ -82,6 +82,31 @@ def test_not_converged_reports_status():
     assert np.isfinite(to_host(x)).all()
 
 
+def test_graph_blocks_and_plain_tail_match_the_oracle():
+    """fem_solve replays blocks of eight PCG iterations as CUDA graphs and runs what is left below the
+    cap as single launches.  With a cap of 13 iterations (one block, then five single iterations) the
+    FP64 iterate equals the oracle's Jacobi-PCG after 13 iterations, and the allocation-free solve
+    (single launches throughout) gives the same iterate."""
+    p = 2
+    sp, xyz, cells, dofs, keys, mask = setup_problem(6, p)
+    perm = sp.dof_permutation()
+    b = sp.rhs_const(1.0)
+    b_can = np.empty(sp.n_dofs)
+    b_can[perm] = to_host(b)
+    x, st = sp.solve(b, mode="pcg", rtol=1e-15, max_inner=13, raise_on_notconv=False)
+    assert st["inner"] == 13 and not st["converged"]
+    x_can = np.empty(sp.n_dofs)
+    x_can[perm] = to_host(x)
+    d = cg.diagonal(xyz, cells, p, sp.n_dofs, dirichlet_mask=mask, dofs=dofs)
+    op = lambda v: cg.apply(xyz, cells, v, p, dirichlet_mask=mask, dofs=dofs)
+    x_ref, it, _ = solve.jacobi_pcg(op, d, b_can, rtol=0.0, maxiter=13)
+    assert it == 13
+    assert np.linalg.norm(x_can - x_ref) <= 1e-10 * np.linalg.norm(x_ref)
+    x2, st2 = sp.solve(b, mode="pcg", rtol=1e-15, max_inner=13, raise_on_notconv=False, no_alloc=True)
+    assert st2["inner"] == 13
+    assert torch.allclose(x, x2, rtol=1e-12, atol=1e-14)
+
+
 def test_zero_rhs_and_initial_guess():
     sp, *_ = setup_problem(3, 2)
     b = torch.zeros(sp.n_dofs, dtype=torch.float64, device="cuda")
