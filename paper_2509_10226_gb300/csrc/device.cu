@@ -32,6 +32,68 @@ int sm_count() {
 
 namespace {
 
+// Places a tile's groups in its shared-memory staging: group q of the sorted list goes to the
+// 16-byte slot sig[q] (4 words, banks 4 (slot mod 8) .. 4 (slot mod 8) + 3), and the list is stored
+// in slot order.  The row build reads node j of a warp's 32 cells with one instruction and the
+// pre-reduction adds to them with one more; two distinct groups in the same bank group whose DoFs
+// have the same remainder mod 4 fall in one bank and cost an extra shared-memory wavefront.  Slots
+// stay inside windows of 8 consecutive groups of the sorted list, so a warp's 32 consecutive list
+// entries are the same groups as before and touch the same memory sectors.  Inside a window the
+// groups take the 8 bank groups greedily, the most-met group first, each the free bank group
+// where it meets the fewest groups already placed.
+const std::vector<int32_t>& bank_slots(const Ctx& c, int64_t e0, int64_t e1, const std::vector<int32_t>& buf,
+                                       std::vector<std::vector<int32_t>>& adj, std::vector<int32_t>& order,
+                                       std::vector<int32_t>& sig) {
+  const int L = int(buf.size());
+  if (int(adj.size()) < L) adj.resize(size_t(L));
+  for (int q = 0; q < L; ++q) adj[size_t(q)].clear();
+  // pairs of distinct groups met by one warp instruction in the same bank (DoF mod 4), once per
+  // instruction
+  int32_t seen[4][32];
+  for (int64_t w0 = e0; w0 < e1; w0 += 32) {
+    const int64_t w1 = std::min<int64_t>(e1, w0 + 32);
+    for (int j = 0; j < c.nd; ++j) {
+      int cnt[4] = {0, 0, 0, 0};
+      for (int64_t e = w0; e < w1; ++e) {
+        const int32_t d = c.cell_dofs[size_t(e) * c.nd + j];
+        if (c.mask[d]) continue;
+        const int32_t q = int32_t(std::lower_bound(buf.begin(), buf.end(), d / 4) - buf.begin());
+        const int k = d & 3;
+        bool dup = false;
+        for (int i = 0; i < cnt[k]; ++i) dup |= seen[k][i] == q;
+        if (dup) continue;
+        for (int i = 0; i < cnt[k]; ++i) {
+          adj[size_t(q)].push_back(seen[k][i]);
+          adj[size_t(seen[k][i])].push_back(q);
+        }
+        seen[k][cnt[k]++] = q;
+      }
+    }
+  }
+  sig.assign(size_t(L), -1);
+  for (int w = 0; w < L; w += 8) {
+    const int n = std::min(8, L - w);
+    order.clear();
+    for (int q = w; q < w + n; ++q) order.push_back(q);
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+      const size_t da = adj[size_t(a)].size(), db = adj[size_t(b)].size();
+      return da > db || (da == db && a < b);
+    });
+    unsigned used = 0;
+    for (const int q : order) {
+      int cost[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (const int32_t o : adj[size_t(q)])
+        if (sig[size_t(o)] >= 0) ++cost[sig[size_t(o)] & 7];
+      int best = -1;
+      for (int k = 0; k < n; ++k)
+        if (!((used >> k) & 1u) && (best < 0 || cost[k] < cost[best])) best = k;
+      used |= 1u << best;
+      sig[size_t(q)] = w + best;
+    }
+  }
+  return sig;
+}
+
 template <typename T>
 int dalloc(Ctx& c, T** p, size_t n) {
   *p = nullptr;
@@ -80,9 +142,10 @@ int upload(Ctx& c) {
     }
     if (int s = put(c, &c.d_idx, idx)) return s;
     // tile-local lists: the tensor-core kernels move each tile's values in whole 16-byte groups
-    // of 4 consecutive DoFs (group g = DoFs 4g .. 4g+3).  Per tile: the sorted distinct groups that
-    // hold its unconstrained DoFs, and per (cell, local node) the node's position in the tile's
-    // staging, 4 x (the group's place in the list) + (DoF mod 4).  The DoF numbering (by the set of
+    // of 4 consecutive DoFs (group g = DoFs 4g .. 4g+3).  Per tile: the distinct groups that hold
+    // its unconstrained DoFs, in the order of their staging slots (sorted, then permuted inside
+    // windows of 8 by bank_slots), and per (cell, local node) the node's position in the tile's
+    // staging, 4 x (the group's slot) + (DoF mod 4).  The DoF numbering (by the set of
     // tiles sharing a DoF) makes these groups dense: about 4 of every 4.3 staged values are used.
     std::vector<int64_t> span(size_t(c.ntiles) * 2, 0);
     std::vector<int32_t> list;
@@ -91,7 +154,8 @@ int upload(Ctx& c) {
     // in the list), a 4-value slot the kernel keeps at zero on gather and never flushes
     const int ndp = (c.nd + 1) / 2 * 2;
     std::vector<uint16_t> lidx(size_t(c.ntiles) * ndp * T, 0);
-    std::vector<int32_t> buf;
+    std::vector<int32_t> buf, placed, order, sig;
+    std::vector<std::vector<int32_t>> adj;
     list.reserve(size_t(c.nc) * 2);
     for (int64_t t = 0; t < c.ntiles; ++t) {
       buf.clear();
@@ -109,18 +173,21 @@ int upload(Ctx& c) {
       }
       std::fill(lidx.begin() + size_t(t) * ndp * T, lidx.begin() + size_t(t + 1) * ndp * T,
                 uint16_t(4 * buf.size()));
+      const std::vector<int32_t>& slot = bank_slots(c, t * T, e1, buf, adj, order, sig);
       for (int64_t e = t * T; e < e1; ++e)
         for (int j = 0; j < c.nd; ++j) {
           const int32_t d = c.cell_dofs[size_t(e) * c.nd + j];
           if (c.mask[d]) continue;
           const size_t pos = std::lower_bound(buf.begin(), buf.end(), d / 4) - buf.begin();
           lidx[size_t(t) * ndp * T + ((size_t(j) / 2) * T + (e - t * T)) * 2 + (j & 1)] =
-              uint16_t(4 * pos + (d & 3));
+              uint16_t(4 * slot[pos] + (d & 3));
         }
       c.tl_max = std::max<int32_t>(c.tl_max, int32_t(buf.size()));
       span[2 * t] = int64_t(list.size());
       span[2 * t + 1] = int64_t(buf.size());
-      list.insert(list.end(), buf.begin(), buf.end());
+      placed.assign(buf.size(), 0);
+      for (size_t q = 0; q < buf.size(); ++q) placed[size_t(slot[q])] = buf[q];
+      list.insert(list.end(), placed.begin(), placed.end());
       while (list.size() % 4) list.push_back(buf.empty() ? 0 : buf.back());  // 16-byte aligned lists
     }
     if (int s = put(c, &c.d_tl_span, span)) return s;
