@@ -560,7 +560,9 @@ def main():
     y_head = y32.double().clone()
     hb = cg_bytes(C, N, nd, head)
     achieved = hb / (t_head * 1e-3) / 1e9
-    traffic = profiled_traffic(["cg_tc.cu", "tc_ptx.cuh"], "k_cg_apply_tc.cg_p3_64.md") if n == 64 else None
+    # the capture belongs to the kernel sources and to the tile lists' layout built in device.cu
+    traffic = (profiled_traffic(["cg_tc.cu", "tc_ptx.cuh", "device.cu"], "k_cg_apply_tc.cg_p3_64.md")
+               if n == 64 else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "algorithmic_bytes": hb,
                 "kernel": "fem_apply tf32 (zero-fill + k_cg_apply_tc_ws)",
