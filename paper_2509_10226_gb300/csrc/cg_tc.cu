@@ -14,9 +14,11 @@
 // unity); it is exact for exact tables and keeps rounded TF32/BF16 tables
 // consistent (constants map to zero, operand error relative to the gradient).
 //
-// Data movement: each 128-cell tile carries the sorted list of the distinct
-// 16-byte groups (4 consecutive DoFs) that hold its unconstrained DoFs and, per
-// (cell, local node), a 16-bit position in the tile's staging.  Set-up numbers
+// Data movement: each 128-cell tile carries the list of the distinct 16-byte
+// groups (4 consecutive DoFs) that hold its unconstrained DoFs, in the order of
+// their staging slots (sorted, then permuted inside windows of 8 to spread a
+// warp's shared-memory accesses over the banks) and, per (cell, local node), a
+// 16-bit position in the tile's staging.  Set-up numbers
 // the DoFs by the set of tiles sharing them, so a tile's DoFs fill its groups
 // densely (at P3 about 880 DoFs in 240 groups).  The values are gathered with
 // one 16-byte cp.async per group, and the tile's contributions are pre-reduced
