@@ -180,9 +180,6 @@ __global__ void __launch_bounds__(kT) k_dg_face_boundary(const int32_t* __restri
                                                          T* __restrict__ y, int64_t nf) {
   extern __shared__ __align__(16) unsigned char smem[];
   const FaceTables<ND, NQF, T> tb = load_face_tables<ND, NQF, T>(smem, Vf, Ef, wf, fperm);
-  // launched early after the tensor-core face kernel, it adds to y only once that kernel is done
-  // (without an early launch this returns at once)
-  asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
   const int64_t f = blockIdx.x * int64_t(kT) + threadIdx.x;
   if (f >= nf) return;
@@ -236,19 +233,6 @@ int launch_dg(Ctx& c, const T* u, T* y, const T* metric, const T* tab, const T* 
   return FEM_OK;
 }
 
-template <int ND, int NQF>
-int launch_boundary32(Ctx& c, const float* u, float* y, cudaStream_t st) {
-  if (c.nfb == 0) return FEM_OK;
-  const TableLayout L = tables_layout(c.tab);
-  const size_t sm_face = (size_t(4) * NQF * ND * 4 + NQF) * sizeof(float) + 6 * NQF * sizeof(int);
-  if (int e = allow_smem(k_dg_face_boundary<ND, NQF, float>, sm_face)) return e;
-  // may start while the tensor-core face kernel runs (the kernel waits for it before adding to y)
-  TETMF_CK(launch_early(k_dg_face_boundary<ND, NQF, float>, dim3(unsigned((c.nfb + kT - 1) / kT)), dim3(kT), sm_face,
-                        st, c.d_fb_cell, c.d_fb_code, c.d_fb_geo32, c.d_tab32 + L.Vf, c.d_tab32 + L.Ef,
-                        c.d_tab32 + L.wf, c.d_fperm, u, y, c.nfb));
-  TETMF_LAUNCH_CK();
-  return FEM_OK;
-}
 
 }  // namespace
 
@@ -262,9 +246,5 @@ int dg_apply(Ctx& c, int prec, const void* u, void* y, void* stream) {
                                                         c.d_metric32, c.d_tab32, c.d_fi_geo32, c.d_fb_geo32, st)))
 }
 
-int dg_boundary_fp32(Ctx& c, const float* u, float* y, void* stream) {
-  cudaStream_t st = as_stream(stream);
-  TETMF_DISPATCH_SPACE(c.p, c.nq, (launch_boundary32<ND, NQF>(c, u, y, st)))
-}
 
 }  // namespace tetmf

@@ -5,26 +5,31 @@
 // DoFs, 128 cells per tile, difference form, Q in TMEM; y is written once per
 // cell (no atomics).
 //
-// Face loop (k_dg_face_tc): interior faces are grouped at set-up into tiles of
-// 128 faces that share the local face index of each side and the orientation
-// (96 combinations), so every face of a tile uses the same reference tables
-// (faces of equal orientation can share their interpolation matrices, Sec. 3.1);
-// groups are padded with faces of zero weight.  Per tile:
-//   1. rows of U- and U+ (both sides' DoFs, shifted by the minus side's first
-//      DoF so that rounded tables keep jumps of smooth fields small: jumps and
-//      gradients are unchanged by a common shift);
+// Face loop (k_dg_face_tc): faces in tiles of 128, in the Morton order of their
+// minus cells (padded with faces of zero weight).  Each side's cell is relabelled
+// so that the face is its local face 0 with the face's vertices in increasing
+// global order: both sides then place the face points alike, and one evaluation
+// and one integration table serve every face (faces of equal orientation can
+// share their interpolation matrices, Sec. 3.1; here every face is brought to
+// one orientation).  The relabelling only permutes a cell's DoFs (one of 24
+// permutations).  Per tile:
+//   1. rows of U- and U+ (both sides' DoFs in relabelled order, shifted by the
+//      minus side's first DoF so that rounded tables keep jumps of smooth fields
+//      small: jumps and gradients are unchanged by a common shift);
 //   2. two GEMMs evaluate value and reference gradient at the face points:
-//      D = U . T^T with T = [phi; d phi / d xhat] (4 nqf x nd); the plus side's
-//      table has its points permuted into the minus side's order;
+//      D = U . T^T with T = [phi; d phi / d xhat] (4 nqf x nd);
 //   3. per face and point the SIPG flux in FP32: jump, average normal
-//      derivative (a . grad_hat with a = J^-1 n), penalty; the coefficients of
-//      the test functions (value, and a * coefficient of the normal
-//      derivative) overwrite D in TMEM;
+//      derivative (a . grad_hat with a = J'^-1 n in each relabelled frame),
+//      penalty; the coefficients of the test functions (value, and a *
+//      coefficient of the normal derivative) overwrite D in TMEM;
 //   4. two GEMMs integrate back, Y = Q . (w T) (weights folded in the table);
-//   5. both rows are added to y with vector atomics.
+//   5. both rows, back in the cells' own DoF order, are added to y with vector
+//      reductions.
 // The rows of U live in TMEM (the A operand of the evaluation GEMMs), and the
 // DoF values and face data of the next tiles are copied ahead (cp.async).
-// Boundary faces (2 % of the faces at 48^3) keep the FP32 SIMT kernel.
+// Boundary faces take the mirror state of the weak Dirichlet condition (u+ = -u-, equal normal
+// derivatives) and go through the same tiles: their plus row is the negated minus row, with
+// a+ = -a-, and only their minus side is added to y.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -273,6 +278,7 @@ __global__ void __launch_bounds__(kT * cell_gmax<ND, NQ, BF16>(), 1)
 
 // ---- interior faces ---------------------------------------------------------
 constexpr int kMetaWords = 11 * kTile;  // one slot of face data (see issue_face_meta)
+constexpr int32_t kMirrorFace = 1 << 16;  // relabelling word: a boundary face (mirror state on its plus side)
 
 // per warpgroup: the DoF values of both sides (one slot), their results on the way back to y
 // (the rows in the cells' own DoF order) and the face data (two slots); per CTA: the two tables and
@@ -425,8 +431,6 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
   using S = FaceShape<ND, NQF, BF16>;
   constexpr int AW = BF16 ? S::KE / 2 : S::KE;  // TMEM columns of one row of U
   static_assert(AW <= S::NI && AW % 8 == 0, "rows of U must fit in the Y columns");
-  // the boundary-face kernel launched after this one may start now; it waits for this kernel
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   extern __shared__ __align__(1024) uint8_t smem[];
   const int G = blockDim.x / kT;
   const int g = threadIdx.x / kT;
@@ -489,6 +493,7 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
     // face data of the tile: cells of both sides, relabellings, a- a+ 2|F| tau
     const int64_t cm = int32_t(meta[m]), cp = int32_t(meta[kT + m]);
     const uint32_t rl = meta[2 * kT + m];
+    const bool mirror = (rl & uint32_t(kMirrorFace)) != 0;  // boundary face: plus side = -(minus side)
     float geo[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) geo[r] = __uint_as_float(meta[(3 + r) * kT + m]);
@@ -502,7 +507,9 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
       const float* rm = sU + m * ND;
       const float* rp = sU + (kT + m) * ND;
 #pragma unroll
-      for (int j = 0; j < ND; ++j) um[j] = rm[perm_at(wm, j)], up[j] = rp[perm_at(wp, j)];
+      for (int j = 0; j < ND; ++j) um[j] = rm[perm_at(wm, j)];
+#pragma unroll
+      for (int j = 0; j < ND; ++j) up[j] = mirror ? -um[j] : rp[perm_at(wp, j)];
       const float sh = um[0];
       uint32_t w[AW];
       pack_row<ND, S::KE, BF16>(um, sh, w);
@@ -629,7 +636,7 @@ __global__ void __launch_bounds__(kT * FaceShape<ND, NQF, BF16>::GMAX, 1)
       uint32_t v[ND];
 #pragma unroll
       for (int j = 0; j < ND; ++j) v[j] = __float_as_uint(vf[j]);
-      if (geo[6] != 0.0f) red_cell<ND>(y + (side ? cp : cm) * ND, v);
+      if (geo[6] != 0.0f && !(side && mirror)) red_cell<ND>(y + (side ? cp : cm) * ND, v);
     }
     tc_fence_before();
   }
@@ -686,7 +693,7 @@ int launch_dg_tc(Ctx& c, const float* u, float* y, cudaStream_t st) {
                           cols, c.d_status));
     TETMF_LAUNCH_CK();
   }
-  return dg_boundary_fp32(c, u, y, st);
+  return FEM_OK;
 }
 
 }  // namespace
@@ -742,21 +749,30 @@ int dg_tc_prepare(Ctx& c) {
                det;
     }
   };
-  // interior faces in the order of their minus cell (then its local face)
-  std::vector<int64_t> order(c.nfi);
-  for (int64_t i = 0; i < c.nfi; ++i) order[i] = i;
+  // interior faces (index i < nfi) and boundary faces (nfi + b) in the order of their minus cell
+  // (then its local face).  A boundary face takes the mirror state of the weak Dirichlet condition,
+  // u+ = -u-, d u+ / dn = d u- / dn: its plus side is the minus cell itself with negated values
+  // (flag bit 16 of the relabelling word) and a+ = -a-, so that the interior flux gives the
+  // boundary one, and only its minus side is added to y.
+  const int64_t nf = c.nfi + c.nfb;
+  auto minus_cell = [&](int64_t i) { return i < c.nfi ? c.fi_cell[i] : c.fb_cell[i - c.nfi]; };
+  auto minus_face = [&](int64_t i) { return i < c.nfi ? (c.fi_code[i] & 3) : (c.fb_code[i - c.nfi] & 3); };
+  std::vector<int64_t> order(nf);
+  for (int64_t i = 0; i < nf; ++i) order[i] = i;
   std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-    const int32_t ca = c.fi_cell[a], cb = c.fi_cell[b];
-    return ca < cb || (ca == cb && (c.fi_code[a] & 3) < (c.fi_code[b] & 3));
+    const int32_t ca = minus_cell(a), cb = minus_cell(b);
+    return ca < cb || (ca == cb && minus_face(a) < minus_face(b));
   });
-  const int64_t nt = (c.nfi + kT - 1) / kT;
+  const int64_t nt = (nf + kT - 1) / kT;
   c.dg_ntiles = nt;
   std::vector<int32_t> cell(size_t(nt) * 2 * kT, 0), rl(size_t(nt) * kT, 0);
   std::vector<float> geo(size_t(nt) * 8 * kT, 0.0f);
-  for (int64_t r = 0; r < c.nfi; ++r) {
+  for (int64_t r = 0; r < nf; ++r) {
     const int64_t i = order[r], t = r / kT, m = r % kT;
-    const int32_t em = c.fi_cell[i], ep = c.fi_cell[c.nfi + i];
-    const int fm = c.fi_code[i] & 3, fp = (c.fi_code[i] >> 2) & 3;
+    const bool mirror = i >= c.nfi;
+    const int64_t ib = i - c.nfi;
+    const int32_t em = minus_cell(i), ep = mirror ? em : c.fi_cell[c.nfi + i];
+    const int fm = minus_face(i), fp = mirror ? fm : (c.fi_code[i] >> 2) & 3;
     const int32_t* vm = lib_cell(em);
     const int32_t* vp = lib_cell(ep);
     int32_t gv[3] = {vm[kFv[fm][0]], vm[kFv[fm][1]], vm[kFv[fm][2]]};
@@ -782,12 +798,17 @@ int dg_tc_prepare(Ctx& c) {
     for (int k = 0; k < 3; ++k) n[k] *= sgn / len;
     double am[3], ap[3];
     jinv_n(vm, sm, n, am);
-    jinv_n(vp, sp, n, ap);
+    if (mirror) {
+      for (int k = 0; k < 3; ++k) ap[k] = -am[k];
+    } else {
+      jinv_n(vp, sp, n, ap);
+    }
     cell[(size_t(t) * 2 + 0) * kT + m] = em;
     cell[(size_t(t) * 2 + 1) * kT + m] = ep;
-    rl[size_t(t) * kT + m] = perm_id(sm) | (perm_id(sp) << 8);
-    const double g8[8] = {am[0], am[1], am[2], ap[0], ap[1], ap[2], c.fi_geo[size_t(6) * c.nfi + i],
-                          c.fi_geo[size_t(7) * c.nfi + i]};
+    rl[size_t(t) * kT + m] = perm_id(sm) | (perm_id(sp) << 8) | (mirror ? kMirrorFace : 0);
+    const double sF = mirror ? c.fb_geo[size_t(3) * c.nfb + ib] : c.fi_geo[size_t(6) * c.nfi + i];
+    const double tau = mirror ? c.fb_geo[size_t(4) * c.nfb + ib] : c.fi_geo[size_t(7) * c.nfi + i];
+    const double g8[8] = {am[0], am[1], am[2], ap[0], ap[1], ap[2], sF, tau};
     for (int q = 0; q < 8; ++q) geo[(size_t(t) * 8 + q) * kT + m] = float(g8[q]);
   }
   auto up = [&](auto** dst, const auto& v) -> int {

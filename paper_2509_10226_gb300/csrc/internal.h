@@ -91,12 +91,13 @@ struct Ctx {
   void* d_tc_tf32 = nullptr;
   void* d_tc_bf16 = nullptr;
   void* d_tc_tf32x3 = nullptr;      // high then low TF32 parts (3xTF32)
-  // DG tensor-core face loop: interior faces in tiles of 128 faces sharing (f-, f+, orientation)
-  // (faces in the order of their minus cells; each side's cell relabelled so that the face is its
-  // local face 0 with the face's vertices in increasing global order: one pair of tables for all)
+  // DG tensor-core face loop: interior and boundary faces in tiles of 128 faces, in the order of
+  // their minus cells; each side's cell relabelled so that the face is its local face 0 with the
+  // face's vertices in increasing global order (one pair of tables for all); a boundary face has
+  // the minus cell on both sides and its mirror flag set
   int64_t dg_ntiles = 0;
   int32_t* d_dgt_cell = nullptr;    // [dg_ntiles][2][128] minus, plus (padding faces: 0, 0)
-  int32_t* d_dgt_perm = nullptr;    // [dg_ntiles][128] relabelling of each side: minus | plus << 8
+  int32_t* d_dgt_perm = nullptr;    // [dg_ntiles][128] relabelling of each side: minus | plus << 8, 1 << 16 mirror
   float* d_dgt_geo = nullptr;       // [dg_ntiles][8][128] a-(3) a+(3) 2|F| tau, relabelled frames (padding: 0)
   int8_t* d_dg_dperm = nullptr;     // [24][nd rounded up to 16] old local DoF of each new local DoF, per relabelling
   void* d_dg_img_tf32 = nullptr;    // face-0 evaluation and integration tables (2 operand images)
@@ -148,7 +149,6 @@ int solve(Ctx& c, const fem_solve_opts* o, const double* b, double* x, fem_solve
 int tc_prepare(Ctx& c);
 int dg_tc_prepare(Ctx& c);
 int dg_apply_tc(Ctx& c, int prec, const void* u, void* y, void* stream);
-int dg_boundary_fp32(Ctx& c, const float* u, float* y, void* stream);  // adds the boundary-face terms
 int apply_op(Ctx& c, int prec, const void* u, void* y, void* stream);  // y = A u, no coefficient
 int cg_apply_vector_simt(Ctx& c, int prec, int ncomp, const void* u, void* y, void* stream);
 int chebyshev(Ctx& c, int prec, const void* b, void* x, const void* diag, int degree, double lam_max,
