@@ -225,9 +225,10 @@ int fem_fma_probe(int32_t kind, int64_t iters, double* sink, double* flops, void
 /* y = A(k) u.  u, y: device vectors of N values (double for FEM_FP64, float
  * otherwise), library order, must not alias.  k: NULL (k = 1) or device
  * [n_cells][nq] of the vector type.  Eq. 3 (CG), Eq. 5 (DG).  DG supports
- * k = NULL only; its FEM_TF32 / FEM_BF16 path (cell and interior-face products
- * on the tensor cores, boundary faces in FP32) wants u and y 16-byte aligned
- * (EINVAL otherwise).  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+ * k = NULL only; its FEM_TF32 / FEM_BF16 path (cell and face products on the
+ * tensor cores, boundary faces with the mirror state in the same face tiles)
+ * wants u and y 16-byte aligned (EINVAL otherwise).  Errors: EINVAL,
+ * EUNSUPPORTED, ECUDA. */
 int fem_apply(fem_ctx* ctx, int32_t prec, const void* u, void* y, const void* k, void* stream);
 
 /* Vector Laplacian with ncomp (1..8) independent components, y_c = A u_c
